@@ -1,0 +1,160 @@
+"""Seeded synthetic filterbank inputs (shared by the tests, the oracle checks
+and the benchmark).
+
+This module draws inputs only.  It holds none of the de-dispersion
+arithmetic: the per-channel arrival delays of an injected pulse are passed in
+by the caller (the tests take them from the oracle, the benchmark from the
+library's own plan), so neither side's shift rule lives here.
+
+The paper's test data are sigproc simulations of a dispersed pulse in noise
+(Sec. 2, Fig. 1); those files are not available, so every workload below is a
+seeded stand-in with the same structure: Gaussian total-intensity noise per
+(f,t) cell plus broadband square pulses that follow a dispersion curve.
+
+Recipe (all workloads):
+  * noise: FP64 N(128, 16) from numpy's PCG64(seed), drawn row by row
+    (channel-major), so chunked generation gives the same values;
+  * pulses: +amp counts added in FP64 to in[c][t_p + delay[c] + k], k < width;
+  * uint8: round half to even, clip to [0, 255];
+  * float16/float32 "same noise" variants: the uint8 values converted exactly;
+  * "non-integer" variants: the FP64 values clipped to [0, 255] and rounded
+    to float16/float32 (stress cases for the floating-point error bound).
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+
+
+@dataclass(frozen=True)
+class Pulse:
+    dm: float          # trial DM the pulse is dispersed with (pc cm^-3)
+    t: int             # arrival sample at the top of the band
+    width: int         # samples
+    amp: float = 40.0  # counts added per sample
+
+
+@dataclass(frozen=True)
+class Workload:
+    name: str
+    nchan: int
+    fch1: float        # MHz, centre of channel 0
+    foff: float        # MHz, channel step (negative: descending)
+    tsamp: float       # seconds
+    nsamp_out: int     # output samples per DM
+    ndm: int
+    dm_lo: float
+    dm_step: float
+    seed: int
+    pulses: tuple = field(default_factory=tuple)
+    random_pulses: int = 0   # extra pulses drawn from the seed (grid DMs)
+
+    def dm_list(self) -> np.ndarray:
+        """Trial DMs, built in FP64 and handed over as FP32."""
+        return dm_grid(self.dm_lo, self.dm_step, self.ndm)
+
+    def duration_s(self) -> float:
+        return self.nsamp_out * self.tsamp
+
+    def adds(self) -> int:
+        return self.nchan * self.ndm * self.nsamp_out
+
+
+def dm_grid(dm_lo: float, dm_step: float, ndm: int) -> np.ndarray:
+    return (float(dm_lo) + np.arange(ndm, dtype=np.float64) * float(dm_step)).astype(np.float32)
+
+
+# The five workloads of the build, by what they are.
+SMALL = Workload("small-64ch-64dm-8k", nchan=64, fch1=1500.0, foff=-1.0, tsamp=64e-6,
+                 nsamp_out=8192, ndm=64, dm_lo=0.0, dm_step=1.0, seed=1,
+                 pulses=(Pulse(30.0, 2000, 4, 40.0),))
+LBAND = Workload("lband-1024ch-1024dm-131072", nchan=1024, fch1=1500.0, foff=-0.29296875,
+                 tsamp=64e-6, nsamp_out=131072, ndm=1024, dm_lo=0.0, dm_step=1.0, seed=2,
+                 random_pulses=8)
+LOWFREQ = Workload("lowfreq-4096ch-2000dm-262144", nchan=4096, fch1=150.0,
+                   foff=-0.00732421875, tsamp=327.68e-6, nsamp_out=262144, ndm=2000,
+                   dm_lo=0.0, dm_step=0.05, seed=3,
+                   pulses=(Pulse(12.3, 262144 // 3, 4, 40.0),
+                           Pulse(57.8, 2 * 262144 // 3, 4, 40.0)))
+
+WORKLOADS = {w.name: w for w in (SMALL, LBAND, LOWFREQ)}
+
+
+def random_pulses(w: Workload) -> list[Pulse]:
+    """Pulses drawn from the seed: grid DMs, t in [0, nsamp_out - 16), widths 1..16."""
+    rng = np.random.Generator(np.random.PCG64(w.seed + 7919))
+    out = []
+    dms = w.dm_list()
+    for _ in range(w.random_pulses):
+        d = int(rng.integers(0, w.ndm))
+        t = int(rng.integers(0, w.nsamp_out - 16))
+        width = int(rng.integers(1, 17))
+        out.append(Pulse(float(dms[d]), t, width, 40.0))
+    return out
+
+
+def all_pulses(w: Workload) -> list[Pulse]:
+    return list(w.pulses) + random_pulses(w)
+
+
+def noise_rows(seed: int, nchan: int, nsamp: int, chunk_rows: int = 64):
+    """Yield (c0, block) with block = FP64 N(128,16) rows c0..c0+len(block)-1."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    for c0 in range(0, nchan, chunk_rows):
+        n = min(chunk_rows, nchan - c0)
+        yield c0, rng.normal(128.0, 16.0, size=(n, nsamp))
+
+
+def add_pulse(block: np.ndarray, c0: int, delays: np.ndarray, pulse: Pulse) -> None:
+    """Add a square pulse to rows c0.. of block; delays[c] is its arrival offset
+    (samples) in channel c relative to the top of the band."""
+    n, nsamp = block.shape
+    for r in range(n):
+        start = pulse.t + int(delays[c0 + r])
+        lo, hi = max(start, 0), min(start + pulse.width, nsamp)
+        if lo < hi:
+            block[r, lo:hi] += pulse.amp
+
+
+def to_u8(block: np.ndarray) -> np.ndarray:
+    return np.clip(np.rint(block), 0.0, 255.0).astype(np.uint8)
+
+
+def filterbank(nchan: int, nsamp_in: int, seed: int, pulses=(), delays=(),
+               kind: str = "u8", pitch: int | None = None) -> np.ndarray:
+    """Seeded (f,t) power array, channel-major [nchan][pitch] (pitch >= nsamp_in;
+    padding samples are zero).
+
+    pulses[i] is dispersed with delays[i] (int array [nchan]).
+    kind: "u8"; "f16"/"f32" (the uint8 values, exactly); "f16-frac"/"f32-frac"
+    (unquantised clipped noise rounded to the storage type).
+    """
+    pitch = nsamp_in if pitch is None else pitch
+    if pitch < nsamp_in:
+        raise ValueError("pitch shorter than the row")
+    dtype = {"u8": np.uint8, "f16": np.float16, "f32": np.float32,
+             "f16-frac": np.float16, "f32-frac": np.float32}[kind]
+    out = np.zeros((nchan, pitch), dtype=dtype)
+    for c0, block in noise_rows(seed, nchan, nsamp_in):
+        for p, dl in zip(pulses, delays):
+            add_pulse(block, c0, dl, p)
+        if kind.endswith("-frac"):
+            out[c0:c0 + len(block), :nsamp_in] = np.clip(block, 0.0, 255.0).astype(dtype)
+        else:
+            out[c0:c0 + len(block), :nsamp_in] = to_u8(block).astype(dtype)
+    return out
+
+
+def random_filterbank(rng: np.random.Generator, nchan: int, nsamp: int, kind: str = "u8",
+                      pitch: int | None = None) -> np.ndarray:
+    """Unstructured random rows for fuzz cases (full uint8 range, or floats)."""
+    pitch = nsamp if pitch is None else pitch
+    if kind == "u8":
+        out = np.zeros((nchan, pitch), dtype=np.uint8)
+        out[:, :nsamp] = rng.integers(0, 256, size=(nchan, nsamp), dtype=np.uint8)
+    else:
+        dt = np.float16 if kind.startswith("f16") else np.float32
+        out = np.zeros((nchan, pitch), dtype=dt)
+        out[:, :nsamp] = rng.uniform(0.0, 255.0, size=(nchan, nsamp)).astype(dt)
+    return out

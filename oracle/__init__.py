@@ -1,0 +1,192 @@
+"""CPU oracle for brute-force incoherent de-dispersion (test infrastructure).
+
+This package is TEST INFRASTRUCTURE.  Only ``tests/``, ``__graft_entry__.smoke``
+and the CPU-baseline leg of ``bench.py`` may import it.  The GPU library
+(``paper_1111_6399_gb300``) never imports, links or runs anything here, and this
+package imports nothing from the library.
+
+The arithmetic lives in ``dedisp_oracle.c`` (plain single-threaded C, built with
+``-ffp-contract=off``); this module only compiles it with gcc and marshals numpy
+arrays through ctypes.  Two builds are made from the same source:
+
+* ``liboracle.so``      -- single-threaded, the oracle proper;
+* ``liboracle_omp.so``  -- the same loops with the DM loop under OpenMP (the
+  "checker" build), used for large parity cases; each (d,t) cell is summed in
+  the same order, so both give identical results.
+
+Definitions follow Sec. 2 of the paper (shift each channel by its dispersion
+delay, then sum over frequency, for every trial DM); the integer shift rule is
+spelled out in the C file's header.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "dedisp_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LOCK = threading.Lock()
+_LIBS: dict[bool, ctypes.CDLL] = {}
+
+_CFLAGS = ["-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared", "-std=c11"]
+
+
+def build(force: bool = False) -> None:
+    """Compile both oracle builds with gcc (seconds)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    for omp in (False, True):
+        out = _lib_path(omp)
+        if not force and os.path.exists(out) and os.path.getmtime(out) >= os.path.getmtime(_SRC):
+            continue
+        cmd = ["gcc", *_CFLAGS, _SRC, "-o", out + ".tmp", "-lm"]
+        if omp:
+            cmd.insert(1, "-fopenmp")
+        subprocess.run(cmd, check=True)
+        os.replace(out + ".tmp", out)
+
+
+def _lib_path(omp: bool) -> str:
+    return os.path.join(_BUILD, "liboracle_omp.so" if omp else "liboracle.so")
+
+
+def _lib(omp: bool = False) -> ctypes.CDLL:
+    with _LOCK:
+        if omp not in _LIBS:
+            build()
+            lib = ctypes.CDLL(_lib_path(omp))
+            p = ctypes.c_void_p
+            i64 = ctypes.c_int64
+            lib.oracle_dmshift.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                           ctypes.c_double, p]
+            lib.oracle_dmshift.restype = ctypes.c_int
+            lib.oracle_shift.argtypes = [ctypes.c_float, ctypes.c_float]
+            lib.oracle_shift.restype = ctypes.c_int
+            lib.oracle_maxshift.argtypes = [ctypes.c_int, p, ctypes.c_int, p]
+            lib.oracle_maxshift.restype = i64
+            lib.oracle_dedisperse_u8.argtypes = [p, ctypes.c_int, i64, p, p, ctypes.c_int,
+                                                 i64, p, i64]
+            lib.oracle_dedisperse_u8.restype = None
+            lib.oracle_half_to_double.argtypes = [ctypes.c_uint16]
+            lib.oracle_half_to_double.restype = ctypes.c_double
+            lib.oracle_dedisperse_float.argtypes = [p, ctypes.c_int, ctypes.c_int, i64, p, p,
+                                                    ctypes.c_int, i64, p, p, i64]
+            lib.oracle_dedisperse_float.restype = None
+            lib.oracle_dedisperse_cells.argtypes = [p, ctypes.c_int, ctypes.c_int, i64, p, p,
+                                                    i64, p, p, p, p]
+            lib.oracle_dedisperse_cells.restype = None
+            _LIBS[omp] = lib
+        return _LIBS[omp]
+
+
+def _ptr(a: np.ndarray) -> int:
+    return a.ctypes.data
+
+
+def dmshift(nchan: int, fch1: float, foff: float, tsamp: float) -> np.ndarray:
+    """FP32 per-channel delay per unit DM, in samples (FP64 evaluation, one rounding)."""
+    out = np.empty(nchan, dtype=np.float32)
+    if _lib().oracle_dmshift(nchan, fch1, foff, tsamp, _ptr(out)) != 0:
+        raise ValueError("invalid band description")
+    return out
+
+
+def shift(dm: float, dmshift_c: float) -> int:
+    """s(c,d) = trunc(float32(dm) * float32(dmshift[c])) with one FP32 multiply."""
+    return int(_lib().oracle_shift(float(np.float32(dm)), float(np.float32(dmshift_c))))
+
+
+def shift_table(dms: np.ndarray, table: np.ndarray) -> np.ndarray:
+    """int32 [ndm][nchan] of s(c,d), one oracle_shift call per cell (small inputs)."""
+    lib = _lib()
+    out = np.empty((len(dms), len(table)), dtype=np.int32)
+    for d, dm in enumerate(np.asarray(dms, dtype=np.float32)):
+        for c, ds in enumerate(np.asarray(table, dtype=np.float32)):
+            out[d, c] = lib.oracle_shift(float(dm), float(ds))
+    return out
+
+
+def maxshift(table: np.ndarray, dms: np.ndarray) -> int:
+    table = np.ascontiguousarray(table, dtype=np.float32)
+    dms = np.ascontiguousarray(dms, dtype=np.float32)
+    return int(_lib().oracle_maxshift(len(table), _ptr(table), len(dms), _ptr(dms)))
+
+
+def half_to_double(bits: int) -> float:
+    return float(_lib().oracle_half_to_double(bits))
+
+
+def dedisperse(data: np.ndarray, table: np.ndarray, dms: np.ndarray, nsamp_out: int,
+               with_abssum: bool = False, threads: bool = False):
+    """Full (DM,t) plane.
+
+    data: [nchan][nsamp_in] uint8, float16 or float32 (C-contiguous rows).
+    uint8 -> float32 plane (exact); float16/float32 -> float64 plane
+    (and, if with_abssum, the float64 plane of sum |in| along each curve).
+    """
+    data = np.ascontiguousarray(data)
+    table = np.ascontiguousarray(table, dtype=np.float32)
+    dms = np.ascontiguousarray(dms, dtype=np.float32)
+    nchan, nsamp_in = data.shape
+    if len(table) != nchan:
+        raise ValueError("dmshift length does not match nchan")
+    if nsamp_in < nsamp_out + maxshift(table, dms):
+        raise ValueError("rows are shorter than nsamp_out + maxshift")
+    lib = _lib(threads)
+    ndm = len(dms)
+    if data.dtype == np.uint8:
+        out = np.empty((ndm, nsamp_out), dtype=np.float32)
+        lib.oracle_dedisperse_u8(_ptr(data), nchan, nsamp_in, _ptr(table), _ptr(dms), ndm,
+                                 nsamp_out, _ptr(out), nsamp_out)
+        return (out, out.astype(np.float64)) if with_abssum else out
+    if data.dtype == np.float16:
+        elem, raw = 2, data.view(np.uint16)
+    elif data.dtype == np.float32:
+        elem, raw = 4, data
+    else:
+        raise TypeError(f"unsupported dtype {data.dtype}")
+    out = np.empty((ndm, nsamp_out), dtype=np.float64)
+    asum = np.empty((ndm, nsamp_out), dtype=np.float64) if with_abssum else None
+    lib.oracle_dedisperse_float(_ptr(raw), elem, nchan, nsamp_in, _ptr(table), _ptr(dms), ndm,
+                                nsamp_out, _ptr(out), _ptr(asum) if asum is not None else None,
+                                nsamp_out)
+    return (out, asum) if with_abssum else out
+
+
+def dedisperse_cells(data: np.ndarray, table: np.ndarray, dms: np.ndarray,
+                     d_idx: np.ndarray, t_idx: np.ndarray, threads: bool = True):
+    """Selected cells (d_idx[i], t_idx[i]) of the plane, for full-size inputs.
+
+    Returns (values, abssum) as float64 arrays; for uint8 the value is the
+    exact FP32 sum widened to float64.
+    """
+    data = np.ascontiguousarray(data)
+    table = np.ascontiguousarray(table, dtype=np.float32)
+    dms = np.ascontiguousarray(dms, dtype=np.float32)
+    d_idx = np.ascontiguousarray(d_idx, dtype=np.int32)
+    t_idx = np.ascontiguousarray(t_idx, dtype=np.int64)
+    nchan, nsamp_in = data.shape
+    if data.dtype == np.uint8:
+        elem, raw = 1, data
+    elif data.dtype == np.float16:
+        elem, raw = 2, data.view(np.uint16)
+    elif data.dtype == np.float32:
+        elem, raw = 4, data
+    else:
+        raise TypeError(f"unsupported dtype {data.dtype}")
+    if len(d_idx) != len(t_idx):
+        raise ValueError("index arrays differ in length")
+    if len(d_idx):
+        need = int(t_idx.max()) + maxshift(table, dms[np.unique(d_idx)])
+        if need >= nsamp_in or d_idx.min() < 0 or d_idx.max() >= len(dms) or t_idx.min() < 0:
+            raise ValueError("cell outside the plane")
+    out = np.empty(len(d_idx), dtype=np.float64)
+    asum = np.empty(len(d_idx), dtype=np.float64)
+    _lib(threads).oracle_dedisperse_cells(_ptr(raw), elem, nchan, nsamp_in, _ptr(table),
+                                          _ptr(dms), len(d_idx), _ptr(d_idx), _ptr(t_idx),
+                                          _ptr(out), _ptr(asum))
+    return out, asum
