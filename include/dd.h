@@ -1,0 +1,153 @@
+/*
+ * dd.h -- C ABI of the GB300 brute-force incoherent de-dispersion library
+ * (libdd.so, built for sm_103a).
+ *
+ * The operation (ARTEMIS paper, Sec. 2): for every trial dispersion measure
+ * d and output sample t,
+ *
+ *     out[d][t] = sum_{c=0}^{nchan-1} in[c][t + s(c,d)]
+ *
+ * where each frequency channel of the (f,t) power array is shifted by its
+ * cold-plasma dispersion delay before the frequency integration.  The shift
+ * rule: dmshift[c] = float(4148.808 * (f_c^-2 - f_top^-2) / tsamp), evaluated
+ * in FP64 on the host with f in MHz and tsamp in seconds, rounded once to
+ * FP32; s(c,d) = (int)(float(dm[d]) * dmshift[c]) with one FP32 multiply
+ * (round to nearest even) and truncation.  f_c = fch1 + c * foff is the
+ * centre frequency of channel c and f_top the highest channel centre.
+ * Sec. 3 of the paper sets the design rules this library follows on GB300:
+ * accumulators in the fastest memory (registers), the (f,t) data staged
+ * close to the SMs (shared memory, filled by the TMA), and as little shift
+ * arithmetic as possible.
+ *
+ * Layouts (Sec. 3, Fig. 2: rows of constant frequency, contiguous time):
+ *   in  : nchan rows, row c at in + c * in_pitch elements; channel 0 is fch1.
+ *         Each row holds at least nsamp_out + maxshift samples.
+ *   out : FP32, ndm rows, row d at out + d * out_pitch floats, in the order of
+ *         the caller's DM list.  Sample t is the arrival time at f_top.
+ * Alignment: in and out 16-byte aligned; in_pitch * element size and
+ * out_pitch * 4 multiples of 16 bytes.
+ *
+ * Accuracy: uint8 input is summed exactly (bit-identical to any exact sum);
+ * FP16/FP32 input is summed in FP32 with compensated block accumulation,
+ * within 1e-6 * sum_c |in[c][t+s(c,d)]| of the exact sum.
+ *
+ * Errors: every call returns a dd_status; a negative status leaves no side
+ * effect on caller memory, and dd_last_error() gives a message (per thread).
+ * Device-side waits are bounded: a wait that runs out records DD_ERR_TIMEOUT
+ * in the plan's device status word, which dd_sync() reports.
+ *
+ * Ownership: the library owns plans, batches and servers (and the device
+ * tables inside them); the caller owns every in/out buffer it passes, which
+ * must stay valid until the work on the given stream has completed.
+ * Streams are passed as void* (a cudaStream_t; NULL is the legacy default
+ * stream).  Plans are immutable after creation and may be used from several
+ * threads and streams at once; a plan's device tables are uploaded lazily,
+ * per device, on its first execution there.
+ */
+#ifndef DD_H
+#define DD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum dd_status {
+    DD_OK = 0,
+    DD_PENDING = 1,         /* dd_poll: the block is still in flight          */
+    DD_ERR_INVALID = -1,    /* bad argument, detected before any launch        */
+    DD_ERR_CUDA = -2,       /* a CUDA runtime call failed                      */
+    DD_ERR_NOMEM = -3,      /* device or pinned-host allocation failed         */
+    DD_ERR_BUSY = -4,       /* dd_submit: no slot or HBM budget free right now */
+    DD_ERR_TIMEOUT = -5,    /* a bounded device wait ran out                   */
+    DD_ERR_DEVICE = -6      /* the kernel recorded an internal check failure   */
+} dd_status;
+
+typedef enum dd_dtype { DD_U8 = 0, DD_F16 = 1, DD_F32 = 2 } dd_dtype;
+
+typedef struct dd_plan_s *dd_plan_t;
+
+/* Tile shape of the de-dispersion kernel (chosen by the plan or the autotuner).
+ *   dm_per_thread    trial DMs each thread accumulates (register accumulators)
+ *   dm_warps         warps of a CTA along the DM axis
+ *   time_warps       warps of a CTA along the time axis
+ *   chan_per_stage   channels staged in shared memory per pipeline stage
+ * A CTA covers dm_per_thread*dm_warps DMs and time_warps*span samples, where
+ * span = 1024 (uint8), 512 (FP16) or 256 (FP32) samples per warp. */
+typedef struct dd_tiles {
+    int dm_per_thread;
+    int dm_warps;
+    int time_warps;
+    int chan_per_stage;
+} dd_tiles;
+
+/* --- plan (Sec. 2: the dispersion law and the trial-DM grid) ------------- */
+
+/* Build a plan: the FP64->FP32 dmshift table, the caller's FP32 DM list and
+ * maxshift = max_{c,d} s(c,d).  Host-only; no GPU is touched.
+ *   nchan >= 1; foff != 0 (MHz, negative for a descending band);
+ *   fch1 (MHz) centre of channel 0; every channel centre must be > 0;
+ *   tsamp > 0 (seconds); dm_list: ndm >= 1 finite values >= 0, any order
+ *   (copied).
+ * Returns DD_ERR_INVALID on a bad argument, DD_ERR_NOMEM if out of memory. */
+dd_status dd_plan(int nchan, double fch1_mhz, double foff_mhz, double tsamp_s,
+                  const float *dm_list, int ndm, dd_plan_t *plan_out);
+
+/* Free a plan and its device tables (NULL is a no-op).  No work using the
+ * plan may still be in flight. */
+void dd_plan_destroy(dd_plan_t plan);
+
+int64_t dd_plan_maxshift(dd_plan_t plan);   /* -1 on NULL */
+int dd_plan_nchan(dd_plan_t plan);          /* -1 on NULL */
+int dd_plan_ndm(dd_plan_t plan);            /* -1 on NULL */
+
+/* Copy the FP32 dmshift table (nchan floats) to host memory. */
+dd_status dd_plan_dmshift(dd_plan_t plan, float *host_out);
+
+/* Tile shape the plan uses for dtype (default heuristic unless set).  */
+dd_status dd_plan_get_tiles(dd_plan_t plan, dd_dtype dtype, dd_tiles *tiles_out);
+
+/* Override the tile shape for dtype (validated: shared-memory fit, supported
+ * dm_per_thread).  Not thread-safe against concurrent executions of the plan. */
+dd_status dd_plan_set_tiles(dd_plan_t plan, dd_dtype dtype, const dd_tiles *tiles);
+
+/* --- single-beam execution (Sec. 3: the GPU kernel) ---------------------- */
+
+/* De-disperse one beam, asynchronously on stream.
+ *   in        device pointer to nchan rows (dtype elements, in_pitch apart)
+ *   nsamp_in  valid samples per input row; must be >= nsamp_out + maxshift
+ *   out       device pointer to ndm FP32 rows, out_pitch floats apart
+ *   nsamp_out output samples per DM (>= 0; 0 is a no-op)
+ * Validation (DD_ERR_INVALID, nothing launched): alignment rules above,
+ * in_pitch >= nsamp_in, out_pitch >= nsamp_out, nsamp_in large enough.
+ * The first call on a device uploads the plan's tables (synchronous copy). */
+dd_status dd_execute(dd_plan_t plan, const void *in, dd_dtype dtype, int64_t in_pitch,
+                     int64_t nsamp_in, float *out, int64_t out_pitch, int64_t nsamp_out,
+                     void *stream);
+
+/* End-to-end form on HOST buffers (pinned or pageable): copies the input in
+ * time blocks to library-owned device buffers, de-disperses each block and
+ * copies the plane back, overlapping copies and kernels on two streams.
+ * Synchronous: returns when out_host is complete.  Layouts as dd_execute,
+ * with pitches in elements of host rows (no alignment rule on host rows). */
+dd_status dd_execute_host(dd_plan_t plan, const void *in_host, dd_dtype dtype,
+                          int64_t in_pitch, int64_t nsamp_in, float *out_host,
+                          int64_t out_pitch, int64_t nsamp_out);
+
+/* Synchronize stream and report the plan's device status word (DD_OK,
+ * DD_ERR_TIMEOUT or DD_ERR_DEVICE), then clear it. */
+dd_status dd_sync(dd_plan_t plan, void *stream);
+
+/* Kernel launches made by this process so far (all entry points). */
+int64_t dd_launch_count(void);
+
+/* Message for the last non-OK status returned on this thread. */
+const char *dd_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DD_H */

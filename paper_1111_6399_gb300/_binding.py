@@ -1,0 +1,204 @@
+"""ctypes binding of libdd.so (argument marshalling only).
+
+Every step of the de-dispersion path runs in the CUDA library; this module
+converts Python/numpy/torch arguments to plain pointers and sizes and raises
+on a non-OK status.  It never falls back to another implementation: if the
+library is missing or fails to load, importing the package raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libdd.so")
+
+DD_U8, DD_F16, DD_F32 = 0, 1, 2
+STATUS = {0: "DD_OK", 1: "DD_PENDING", -1: "DD_ERR_INVALID", -2: "DD_ERR_CUDA",
+          -3: "DD_ERR_NOMEM", -4: "DD_ERR_BUSY", -5: "DD_ERR_TIMEOUT", -6: "DD_ERR_DEVICE"}
+DD_OK, DD_PENDING, DD_ERR_INVALID, DD_ERR_CUDA = 0, 1, -1, -2
+DD_ERR_NOMEM, DD_ERR_BUSY, DD_ERR_TIMEOUT, DD_ERR_DEVICE = -3, -4, -5, -6
+
+# Every symbol include/dd.h declares (checked by the tests).
+EXPORTS = [
+    "dd_plan", "dd_plan_destroy", "dd_plan_maxshift", "dd_plan_nchan", "dd_plan_ndm",
+    "dd_plan_dmshift", "dd_plan_get_tiles", "dd_plan_set_tiles", "dd_execute",
+    "dd_execute_host", "dd_sync", "dd_launch_count", "dd_last_error",
+]
+
+
+class DDError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Tiles(ctypes.Structure):
+    _fields_ = [("dm_per_thread", ctypes.c_int), ("dm_warps", ctypes.c_int),
+                ("time_warps", ctypes.c_int), ("chan_per_stage", ctypes.c_int)]
+
+    def as_tuple(self):
+        return (self.dm_per_thread, self.dm_warps, self.time_warps, self.chan_per_stage)
+
+
+def _load() -> ctypes.CDLL:
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"libdd.so not built ({LIB_PATH}); run "
+                          "python -m paper_1111_6399_gb300.build")
+    lib = ctypes.CDLL(LIB_PATH)
+    p, i64, i32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int
+    sig = {
+        "dd_plan": (i32, [i32, ctypes.c_double, ctypes.c_double, ctypes.c_double, p, i32,
+                          ctypes.POINTER(p)]),
+        "dd_plan_destroy": (None, [p]),
+        "dd_plan_maxshift": (i64, [p]),
+        "dd_plan_nchan": (i32, [p]),
+        "dd_plan_ndm": (i32, [p]),
+        "dd_plan_dmshift": (i32, [p, p]),
+        "dd_plan_get_tiles": (i32, [p, i32, ctypes.POINTER(Tiles)]),
+        "dd_plan_set_tiles": (i32, [p, i32, ctypes.POINTER(Tiles)]),
+        "dd_execute": (i32, [p, p, i32, i64, i64, p, i64, i64, p]),
+        "dd_execute_host": (i32, [p, p, i32, i64, i64, p, i64, i64]),
+        "dd_sync": (i32, [p, p]),
+        "dd_launch_count": (i64, []),
+        "dd_last_error": (ctypes.c_char_p, []),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
+lib = _load()
+
+
+def check(status: int) -> int:
+    if status < 0:
+        raise DDError(status, lib.dd_last_error().decode(errors="replace"))
+    return status
+
+
+def dtype_code(dtype) -> int:
+    """numpy / torch dtype (or 'u8'/'f16'/'f32') -> dd_dtype."""
+    name = str(dtype).replace("torch.", "")
+    table = {"uint8": DD_U8, "u8": DD_U8, "float16": DD_F16, "f16": DD_F16,
+             "float32": DD_F32, "f32": DD_F32}
+    if name not in table:
+        raise TypeError(f"unsupported input dtype {dtype}")
+    return table[name]
+
+
+def elem_size(code: int) -> int:
+    return (1, 2, 4)[code]
+
+
+def warp_span(code: int) -> int:
+    return (1024, 512, 256)[code]
+
+
+def launch_count() -> int:
+    return int(lib.dd_launch_count())
+
+
+class Plan:
+    """dd_plan: the host plan (FP64 delay table rounded to FP32, DM list, maxshift)."""
+
+    def __init__(self, nchan: int, fch1: float, foff: float, tsamp: float, dm_list):
+        dms = np.ascontiguousarray(dm_list, dtype=np.float32)
+        h = ctypes.c_void_p()
+        check(lib.dd_plan(int(nchan), float(fch1), float(foff), float(tsamp),
+                          dms.ctypes.data, len(dms), ctypes.byref(h)))
+        self._h = h
+
+    @property
+    def handle(self) -> ctypes.c_void_p:
+        if self._h is None:
+            raise ValueError("plan destroyed")
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None) is not None:
+            lib.dd_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def maxshift(self) -> int:
+        return int(lib.dd_plan_maxshift(self.handle))
+
+    @property
+    def nchan(self) -> int:
+        return int(lib.dd_plan_nchan(self.handle))
+
+    @property
+    def ndm(self) -> int:
+        return int(lib.dd_plan_ndm(self.handle))
+
+    def dmshift(self) -> np.ndarray:
+        out = np.empty(self.nchan, dtype=np.float32)
+        check(lib.dd_plan_dmshift(self.handle, out.ctypes.data))
+        return out
+
+    def get_tiles(self, dtype) -> tuple:
+        t = Tiles()
+        check(lib.dd_plan_get_tiles(self.handle, dtype_code(dtype), ctypes.byref(t)))
+        return t.as_tuple()
+
+    def set_tiles(self, dtype, dm_per_thread, dm_warps, time_warps, chan_per_stage):
+        t = Tiles(dm_per_thread, dm_warps, time_warps, chan_per_stage)
+        check(lib.dd_plan_set_tiles(self.handle, dtype_code(dtype), ctypes.byref(t)))
+
+    # -- execution --------------------------------------------------------
+    def execute_ptr(self, in_ptr: int, dtype: int, in_pitch: int, nsamp_in: int,
+                    out_ptr: int, out_pitch: int, nsamp_out: int, stream: int = 0):
+        """dd_execute on raw device pointers (asynchronous on stream)."""
+        check(lib.dd_execute(self.handle, ctypes.c_void_p(in_ptr), dtype, in_pitch, nsamp_in,
+                             ctypes.c_void_p(out_ptr), out_pitch, nsamp_out,
+                             ctypes.c_void_p(stream)))
+
+    def execute(self, inp, out, nsamp_in: int | None = None, nsamp_out: int | None = None,
+                stream=None):
+        """dd_execute on torch CUDA tensors: inp [nchan][pitch] (uint8/float16/float32),
+        out [ndm][pitch] float32.  Asynchronous on stream (default: torch's current)."""
+        import torch
+        if not (inp.is_cuda and out.is_cuda):
+            raise ValueError("dd_execute takes CUDA tensors; use execute_host for host arrays")
+        if inp.dim() != 2 or out.dim() != 2 or inp.stride(1) != 1 or out.stride(1) != 1:
+            raise ValueError("inp and out must be 2-D with contiguous rows")
+        if out.dtype != torch.float32:
+            raise TypeError("out must be float32")
+        nsamp_in = inp.shape[1] if nsamp_in is None else nsamp_in
+        nsamp_out = out.shape[1] if nsamp_out is None else nsamp_out
+        s = torch.cuda.current_stream(inp.device) if stream is None else stream
+        self.execute_ptr(inp.data_ptr(), dtype_code(inp.dtype), inp.stride(0), nsamp_in,
+                         out.data_ptr(), out.stride(0), nsamp_out, s.cuda_stream)
+
+    def execute_host(self, inp: np.ndarray, out: np.ndarray, nsamp_in: int | None = None,
+                     nsamp_out: int | None = None):
+        """dd_execute_host on host arrays (numpy or CPU torch tensors, pinned or not)."""
+        inp_np = inp.numpy() if hasattr(inp, "numpy") and not isinstance(inp, np.ndarray) else inp
+        out_np = out.numpy() if hasattr(out, "numpy") and not isinstance(out, np.ndarray) else out
+        if inp_np.ndim != 2 or out_np.ndim != 2 or inp_np.strides[1] != inp_np.itemsize \
+                or out_np.strides[1] != 4 or out_np.dtype != np.float32:
+            raise ValueError("inp/out must be 2-D with contiguous rows; out float32")
+        code = dtype_code(inp_np.dtype)
+        nsamp_in = inp_np.shape[1] if nsamp_in is None else nsamp_in
+        nsamp_out = out_np.shape[1] if nsamp_out is None else nsamp_out
+        check(lib.dd_execute_host(self.handle, inp_np.ctypes.data, code,
+                                  inp_np.strides[0] // inp_np.itemsize, nsamp_in,
+                                  out_np.ctypes.data, out_np.strides[0] // 4, nsamp_out))
+
+    def sync(self, stream=None) -> None:
+        """dd_sync: synchronize the stream and raise if a kernel recorded a failure."""
+        h = 0
+        if stream is not None:
+            h = stream if isinstance(stream, int) else stream.cuda_stream
+        check(lib.dd_sync(self.handle, ctypes.c_void_p(h)))

@@ -1,0 +1,99 @@
+"""Build libdd.so in-tree for sm_103a (no cmake; a few translation units in
+parallel).
+
+    python -m paper_1111_6399_gb300.build        # or build() from Python
+
+Outputs paper_1111_6399_gb300/_build/libdd.so.  Host sources are compiled by
+g++ with -ffp-contract=off (the FP64 delay table must not be contracted into
+fused multiply-adds); CUDA sources by nvcc for sm_103a only.
+"""
+from __future__ import annotations
+
+import concurrent.futures as cf
+import glob
+import os
+import shutil
+import subprocess
+import sys
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+CSRC = os.path.join(HERE, "csrc")
+BUILD = os.path.join(HERE, "_build")
+LIB = os.path.join(BUILD, "libdd.so")
+INCLUDE = os.path.join(os.path.dirname(HERE), "include")
+
+
+def _cuda_home() -> str:
+    home = os.environ.get("CUDA_HOME") or os.environ.get("CUDA_PATH")
+    if home and os.path.isdir(home):
+        return home
+    nvcc = shutil.which("nvcc")
+    if nvcc:
+        return os.path.dirname(os.path.dirname(os.path.realpath(nvcc)))
+    return "/usr/local/cuda"
+
+
+def _sources():
+    cu = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
+    cpp = sorted(glob.glob(os.path.join(CSRC, "*.cpp")))
+    return cu, cpp
+
+
+def _headers():
+    return sorted(glob.glob(os.path.join(CSRC, "*.h"))) + sorted(glob.glob(os.path.join(INCLUDE, "*.h")))
+
+
+def _stale(out: str, deps) -> bool:
+    if not os.path.exists(out):
+        return True
+    t = os.path.getmtime(out)
+    return any(os.path.getmtime(d) > t for d in deps)
+
+
+def build(force: bool = False, verbose: bool = False) -> str:
+    cuda = _cuda_home()
+    nvcc = os.path.join(cuda, "bin", "nvcc")
+    cu, cpp = _sources()
+    hdr = _headers()
+    os.makedirs(BUILD, exist_ok=True)
+    jobs = []
+    objs = []
+    for src in cu:
+        obj = os.path.join(BUILD, os.path.basename(src) + ".o")
+        objs.append(obj)
+        if force or _stale(obj, [src, *hdr]):
+            jobs.append([nvcc, "-gencode", "arch=compute_103a,code=sm_103a", "-lineinfo", "-O3",
+                         "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off",
+                         "-Xptxas", "-v" if verbose else "-O3",
+                         "-I", INCLUDE, "-c", src, "-o", obj])
+    for src in cpp:
+        obj = os.path.join(BUILD, os.path.basename(src) + ".o")
+        objs.append(obj)
+        if force or _stale(obj, [src, *hdr]):
+            jobs.append(["g++", "-O2", "-std=c++17", "-fPIC", "-ffp-contract=off",
+                         "-fno-fast-math", "-Wall", "-I", INCLUDE,
+                         "-I", os.path.join(cuda, "include"), "-c", src, "-o", obj])
+    if jobs:
+        with cf.ThreadPoolExecutor(max_workers=min(8, len(jobs))) as ex:
+            results = list(ex.map(lambda c: subprocess.run(c, capture_output=True, text=True), jobs))
+        for cmd, r in zip(jobs, results):
+            if verbose or r.returncode != 0:
+                sys.stderr.write(r.stdout + r.stderr)
+            if r.returncode != 0:
+                raise RuntimeError("compile failed: " + " ".join(cmd))
+    if force or jobs or _stale(LIB, objs):
+        libdir = os.path.join(cuda, "lib64")
+        if not os.path.isdir(libdir):
+            libdir = os.path.join(cuda, "lib")
+        cmd = ["g++", "-shared", "-o", LIB + ".tmp", *objs, "-L", libdir, "-lcudart",
+               f"-Wl,-rpath,{libdir}", "-lpthread"]
+        r = subprocess.run(cmd, capture_output=True, text=True)
+        if r.returncode != 0:
+            sys.stderr.write(r.stdout + r.stderr)
+            raise RuntimeError("link failed: " + " ".join(cmd))
+        os.replace(LIB + ".tmp", LIB)
+    return LIB
+
+
+if __name__ == "__main__":
+    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv))

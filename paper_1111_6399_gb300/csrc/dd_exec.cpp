@@ -1,0 +1,205 @@
+// Entry points that run the de-dispersion kernel: dd_execute (device
+// buffers, asynchronous), dd_execute_host (host buffers, pipelined copies)
+// and dd_sync (device status word).
+#include <cuda_runtime_api.h>
+
+#include <algorithm>
+#include <cstring>
+
+#include "dd_internal.h"
+
+namespace {
+
+using dd::fail;
+
+bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
+
+dd_status check_layout(dd_plan_s *p, dd_dtype dtype, int64_t in_pitch, int64_t nsamp_in,
+                       int64_t out_pitch, int64_t nsamp_out, bool device_rows) {
+    if (dtype != DD_U8 && dtype != DD_F16 && dtype != DD_F32)
+        return fail(DD_ERR_INVALID, "unknown dtype");
+    if (nsamp_out < 0 || nsamp_in < 0)
+        return fail(DD_ERR_INVALID, "negative sample count");
+    if (nsamp_out > 0 && nsamp_in < nsamp_out + p->maxshift)
+        return fail(DD_ERR_INVALID, "nsamp_in must be >= nsamp_out + maxshift (" +
+                                        std::to_string(nsamp_out + p->maxshift) + ")");
+    if (in_pitch < nsamp_in || out_pitch < nsamp_out)
+        return fail(DD_ERR_INVALID, "pitch shorter than a row");
+    if (device_rows) {
+        const int64_t elem = dd::elem_size(dtype);
+        if ((in_pitch * elem) % 16 != 0 || out_pitch % 4 != 0)
+            return fail(DD_ERR_INVALID, "row pitches must be multiples of 16 bytes");
+    }
+    return DD_OK;
+}
+
+struct HostWorkspace {
+    int dev = -1;
+    void *in[2] = {nullptr, nullptr};
+    float *out[2] = {nullptr, nullptr};
+    size_t in_bytes = 0, out_bytes = 0;
+    cudaStream_t s[2] = {nullptr, nullptr};
+    cudaEvent_t landed[2] = {nullptr, nullptr};   // slot's input block copied in
+    cudaEvent_t tail_read[2] = {nullptr, nullptr};  // next slot has read this slot's tail
+};
+
+}  // namespace
+
+extern "C" dd_status dd_execute(dd_plan_t p, const void *in, dd_dtype dtype, int64_t in_pitch,
+                                int64_t nsamp_in, float *out, int64_t out_pitch,
+                                int64_t nsamp_out, void *stream) {
+    if (!p)
+        return fail(DD_ERR_INVALID, "plan is NULL");
+    dd_status st = check_layout(p, dtype, in_pitch, nsamp_in, out_pitch, nsamp_out, true);
+    if (st != DD_OK)
+        return st;
+    if (nsamp_out == 0)
+        return DD_OK;
+    if (!in || !out || !aligned16(in) || !aligned16(out))
+        return fail(DD_ERR_INVALID, "in and out must be non-NULL and 16-byte aligned");
+    dd::Geometry g;
+    if ((st = dd::plan_geometry(p, dtype, &g)) != DD_OK)
+        return st;
+    dd::DevTables *dt = nullptr;
+    if ((st = dd::device_tables(p, &dt)) != DD_OK)
+        return st;
+    return dd::launch_dedisperse(p, g, *dt, in, dtype, in_pitch, nsamp_in, out, out_pitch,
+                                 nsamp_out, stream);
+}
+
+extern "C" dd_status dd_sync(dd_plan_t p, void *stream) {
+    if (!p)
+        return fail(DD_ERR_INVALID, "plan is NULL");
+    cudaError_t e = cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess)
+        return fail(DD_ERR_CUDA, std::string("stream synchronize: ") + cudaGetErrorString(e));
+    dd::DevTables *dt = nullptr;
+    dd_status st = dd::device_tables(p, &dt);
+    if (st != DD_OK)
+        return st;
+    int word = 0;
+    if (cudaMemcpy(&word, dt->status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return fail(DD_ERR_CUDA, "status read failed");
+    if (word != dd::kDevOk) {
+        cudaMemset(dt->status, 0, sizeof(int));
+        return word == dd::kDevTimeout
+                   ? fail(DD_ERR_TIMEOUT, "a device wait ran out (copy never completed)")
+                   : fail(DD_ERR_DEVICE, "kernel recorded a failed internal check");
+    }
+    return DD_OK;
+}
+
+// The host form streams the beam through the GPU in output blocks of B
+// samples.  Input block k covers samples [kB, kB + B + S) of every channel;
+// its first S samples are the previous block's last S, so they are copied
+// device-to-device from the other slot and only B new samples per channel
+// cross the host link.  Two slots alternate on two streams, so the input copy
+// of block k+1 overlaps the kernel and output copy of block k.
+extern "C" dd_status dd_execute_host(dd_plan_t p, const void *in_host, dd_dtype dtype,
+                                     int64_t in_pitch, int64_t nsamp_in, float *out_host,
+                                     int64_t out_pitch, int64_t nsamp_out) {
+    static std::mutex ws_mu;
+    static HostWorkspace ws_by_dev[16];
+    if (!p)
+        return fail(DD_ERR_INVALID, "plan is NULL");
+    dd_status st = check_layout(p, dtype, in_pitch, nsamp_in, out_pitch, nsamp_out, false);
+    if (st != DD_OK)
+        return st;
+    if (nsamp_out == 0)
+        return DD_OK;
+    if (!in_host || !out_host)
+        return fail(DD_ERR_INVALID, "NULL host buffer");
+    dd::Geometry g;
+    if ((st = dd::plan_geometry(p, dtype, &g)) != DD_OK)
+        return st;
+    dd::DevTables *dt = nullptr;
+    if ((st = dd::device_tables(p, &dt)) != DD_OK)
+        return st;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 16)
+        return fail(DD_ERR_INVALID, "device index out of range");
+    std::lock_guard<std::mutex> lk(ws_mu);
+    HostWorkspace &ws = ws_by_dev[dev];
+
+    const int64_t elem = dd::elem_size(dtype);
+    const int64_t S = p->maxshift;
+    const int64_t B = std::min<int64_t>(nsamp_out, std::max<int64_t>(65536, 2 * S));
+    const int64_t dpitch_in = ((B + S) * elem + 15) / 16 * 16;   // bytes
+    const int64_t dpitch_out = (B + 3) / 4 * 4;                 // floats
+    const size_t need_in = (size_t)dpitch_in * p->nchan;
+    const size_t need_out = (size_t)dpitch_out * sizeof(float) * p->ndm;
+    if (ws.s[0] == nullptr) {
+        for (int i = 0; i < 2; ++i) {
+            if (cudaStreamCreateWithFlags(&ws.s[i], cudaStreamNonBlocking) != cudaSuccess ||
+                cudaEventCreateWithFlags(&ws.landed[i], cudaEventDisableTiming) != cudaSuccess ||
+                cudaEventCreateWithFlags(&ws.tail_read[i], cudaEventDisableTiming) != cudaSuccess)
+                return fail(DD_ERR_CUDA, "stream/event creation failed");
+        }
+    }
+    if (ws.in_bytes < need_in || ws.out_bytes < need_out) {
+        for (int i = 0; i < 2; ++i) {
+            cudaFree(ws.in[i]);
+            cudaFree(ws.out[i]);
+            ws.in[i] = nullptr;
+            ws.out[i] = nullptr;
+        }
+        ws.in_bytes = ws.out_bytes = 0;
+        for (int i = 0; i < 2; ++i) {
+            if (cudaMalloc(&ws.in[i], need_in) != cudaSuccess ||
+                cudaMalloc((void **)&ws.out[i], need_out) != cudaSuccess) {
+                cudaGetLastError();
+                return fail(DD_ERR_NOMEM, "device workspace allocation failed");
+            }
+        }
+        ws.in_bytes = need_in;
+        ws.out_bytes = need_out;
+    }
+    const uint8_t *src = static_cast<const uint8_t *>(in_host);
+    const int64_t hpitch_in = in_pitch * elem;
+    const int64_t nblk = (nsamp_out + B - 1) / B;
+    for (int64_t k = 0; k < nblk; ++k) {
+        const int i = (int)(k & 1);
+        cudaStream_t s = ws.s[i];
+        const int64_t t0 = k * B;
+        const int64_t nb = std::min(B, nsamp_out - t0);
+        uint8_t *din = static_cast<uint8_t *>(ws.in[i]);
+        cudaError_t e = cudaSuccess;
+        if (k >= 2)  // the block after the previous user of this slot read its tail
+            e = cudaStreamWaitEvent(s, ws.tail_read[i], 0);
+        if (e == cudaSuccess && k == 0) {
+            e = cudaMemcpy2DAsync(din, dpitch_in, src, hpitch_in, (size_t)((nb + S) * elem),
+                                  p->nchan, cudaMemcpyHostToDevice, s);
+        } else if (e == cudaSuccess) {
+            e = cudaStreamWaitEvent(s, ws.landed[1 - i], 0);
+            if (e == cudaSuccess)
+                e = cudaMemcpy2DAsync(din, dpitch_in,
+                                      static_cast<uint8_t *>(ws.in[1 - i]) + B * elem, dpitch_in,
+                                      (size_t)(S * elem), p->nchan, cudaMemcpyDeviceToDevice, s);
+            if (e == cudaSuccess)
+                e = cudaEventRecord(ws.tail_read[1 - i], s);
+            if (e == cudaSuccess)
+                e = cudaMemcpy2DAsync(din + S * elem, dpitch_in, src + (t0 + S) * elem, hpitch_in,
+                                      (size_t)(nb * elem), p->nchan, cudaMemcpyHostToDevice, s);
+        }
+        if (e == cudaSuccess)
+            e = cudaEventRecord(ws.landed[i], s);
+        if (e != cudaSuccess)
+            return fail(DD_ERR_CUDA, std::string("input copy: ") + cudaGetErrorString(e));
+        st = dd::launch_dedisperse(p, g, *dt, din, dtype, dpitch_in / elem, nb + S, ws.out[i],
+                                   dpitch_out, nb, s);
+        if (st != DD_OK)
+            return st;
+        e = cudaMemcpy2DAsync(out_host + t0, (size_t)out_pitch * sizeof(float), ws.out[i],
+                              (size_t)dpitch_out * sizeof(float), (size_t)nb * sizeof(float),
+                              p->ndm, cudaMemcpyDeviceToHost, s);
+        if (e != cudaSuccess)
+            return fail(DD_ERR_CUDA, std::string("output copy: ") + cudaGetErrorString(e));
+    }
+    for (int i = 0; i < 2; ++i) {
+        cudaError_t e = cudaStreamSynchronize(ws.s[i]);
+        if (e != cudaSuccess)
+            return fail(DD_ERR_CUDA, std::string("synchronize: ") + cudaGetErrorString(e));
+    }
+    return dd_sync(p, nullptr);
+}

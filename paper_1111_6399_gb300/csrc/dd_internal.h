@@ -1,0 +1,96 @@
+// Internal declarations shared by the host plan (dd_plan.cpp) and the CUDA
+// translation units of libdd.  Not part of the public ABI (include/dd.h).
+#pragma once
+
+#include <cstdint>
+#include <map>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/dd.h"
+
+namespace dd {
+
+// Samples covered by one warp along time: 32 lanes x kWords 4-byte words x
+// (4 / element size) samples per word.
+constexpr int kWords = 8;
+inline int elem_size(dd_dtype t) { return t == DD_U8 ? 1 : (t == DD_F16 ? 2 : 4); }
+inline int warp_span(dd_dtype t) { return 32 * kWords * (4 / elem_size(t)); }
+inline int phases(dd_dtype t) { return 4 / elem_size(t); }
+
+// Channels summed into 16-bit SWAR lanes before they are widened (uint8):
+// 256 * 255 = 65280 fits a 16-bit lane.
+constexpr int kSwarChannels = 256;
+// Channels per compensated block for FP16/FP32 input.
+constexpr int kFloatBlock = 64;
+
+constexpr int kMaxSmem = 232448;  // 227 KB dynamic shared memory per CTA
+
+// Device status word values (written by kernels, read by dd_sync).
+constexpr int kDevOk = 0;
+constexpr int kDevTimeout = 1;
+constexpr int kDevCheck = 2;
+
+struct DevTables {
+    float *dmshift = nullptr;    // [nchan]
+    float *dm_sorted = nullptr;  // [ndm_pad]: DMs in ascending order, padded with the last
+    int *perm = nullptr;         // [ndm_pad]: output row of sorted DM k, -1 for padding
+    int *status = nullptr;       // device status word
+    int ndm_pad = 0;
+};
+
+// Launch geometry derived from a tile shape and the plan's tables.
+struct Geometry {
+    dd_tiles tiles{};
+    int elem = 1, nph = 1, span = 0;
+    int dm_cta = 0;       // DMs per CTA
+    int t_cta = 0;        // samples per CTA
+    int ntile_d = 0;      // DM tiles
+    int wp = 0;           // bytes of one phase row in shared memory
+    int smem = 0;         // dynamic shared memory per CTA
+    int threads = 0;
+};
+
+}  // namespace dd
+
+struct dd_plan_s {
+    int nchan = 0, ndm = 0;
+    double fch1 = 0, foff = 0, tsamp = 0;
+    int64_t maxshift = 0;
+    std::vector<float> dmshift;    // [nchan] FP32 table
+    std::vector<float> dm;         // [ndm] caller order
+    std::vector<int> order;        // sorted position -> caller index
+    std::vector<float> dm_sorted;  // [ndm] ascending
+    dd_tiles tiles[3]{};
+    std::mutex mu;
+    std::map<int, dd::DevTables> dev;      // per CUDA device
+    std::map<uint64_t, dd::Geometry> geo;  // per (dtype, tiles) key
+};
+
+namespace dd {
+
+// Thread-local error message; returns st for chaining.
+dd_status fail(dd_status st, const std::string &msg);
+
+// Default tile shape for a dtype.
+dd_tiles default_tiles(dd_dtype t);
+
+// Validate a tile shape for dtype and compute the launch geometry for the
+// plan (shared-memory window bound over every DM tile and channel).
+dd_status make_geometry(dd_plan_s *p, dd_dtype t, const dd_tiles &tl, Geometry *g);
+
+// Geometry for the plan's current tile shape, cached.
+dd_status plan_geometry(dd_plan_s *p, dd_dtype t, Geometry *g);
+
+// Device tables for the current device, uploaded on first use.
+dd_status device_tables(dd_plan_s *p, DevTables **out);
+
+// Launch the de-dispersion kernel (dd_kernel.cu).
+dd_status launch_dedisperse(dd_plan_s *p, const Geometry &g, const DevTables &dt,
+                            const void *in, dd_dtype dtype, int64_t in_pitch, int64_t nsamp_in,
+                            float *out, int64_t out_pitch, int64_t nsamp_out, void *stream);
+
+void count_launch(int n = 1);
+
+}  // namespace dd

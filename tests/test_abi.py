@@ -1,0 +1,127 @@
+"""C-ABI library: loads, exports every declared symbol, and the host plan and
+argument validation behave -- all without a GPU."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import filterbank as fb
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def dd():
+    from paper_1111_6399_gb300 import build
+    build.build()
+    import paper_1111_6399_gb300 as pkg
+    return pkg
+
+
+def _declared():
+    names = []
+    for h in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if h.endswith(".h"):
+            txt = open(os.path.join(ROOT, "include", h)).read()
+            txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+            names += re.findall(r"\b(dd_\w+)\s*\(", txt)
+    return sorted(set(names))
+
+
+def test_library_exports_every_declared_symbol(dd):
+    declared = _declared()
+    assert "dd_execute" in declared and "dd_plan" in declared
+    lib = ctypes.CDLL(dd._binding.LIB_PATH)
+    for name in declared:
+        assert hasattr(lib, name), name
+    assert sorted(dd._binding.EXPORTS) == sorted(n for n in declared if n in dd._binding.EXPORTS)
+
+
+def test_plan_table_is_bit_identical_to_the_oracle(dd, oracle_lib):
+    for w in (fb.SMALL, fb.LBAND, fb.LOWFREQ):
+        p = dd.Plan(w.nchan, w.fch1, w.foff, w.tsamp, w.dm_list())
+        want = oracle_lib.dmshift(w.nchan, w.fch1, w.foff, w.tsamp)
+        assert np.array_equal(p.dmshift().view(np.uint32), want.view(np.uint32))
+        assert p.maxshift == oracle_lib.maxshift(want, w.dm_list())
+        assert (p.nchan, p.ndm) == (w.nchan, w.ndm)
+
+
+def test_plan_on_random_bands_and_unsorted_dms(dd, oracle_lib):
+    rng = np.random.default_rng(4)
+    for _ in range(30):
+        nchan = int(rng.integers(1, 3000))
+        fch1 = float(rng.uniform(50, 3000))
+        foff = float(rng.choice([-1, 1]) * rng.uniform(1e-4, 0.9 * fch1 / max(nchan, 2)))
+        tsamp = float(rng.uniform(1e-6, 1e-2))
+        dms = rng.uniform(0, 3000, size=int(rng.integers(1, 50))).astype(np.float32)
+        p = dd.Plan(nchan, fch1, foff, tsamp, dms)
+        want = oracle_lib.dmshift(nchan, fch1, foff, tsamp)
+        assert np.array_equal(p.dmshift().view(np.uint32), want.view(np.uint32))
+        assert p.maxshift == oracle_lib.maxshift(want, dms)
+
+
+@pytest.mark.parametrize("args", [
+    (0, 1500.0, -1.0, 64e-6, [0.0]),
+    (8, 1500.0, 0.0, 64e-6, [0.0]),
+    (8, 1500.0, -1.0, 0.0, [0.0]),
+    (8, 1500.0, -1.0, -1e-3, [0.0]),
+    (8, 5.0, -1.0, 64e-6, [0.0]),          # channel centres below zero
+    (8, 1500.0, -1.0, 64e-6, []),
+    (8, 1500.0, -1.0, 64e-6, [1.0, -2.0]),
+    (8, 1500.0, -1.0, 64e-6, [float("nan")]),
+    (8, 1500.0, -1.0, 64e-6, [float("inf")]),
+])
+def test_invalid_plans_are_rejected(dd, args):
+    with pytest.raises(dd.DDError) as e:
+        dd.Plan(*args)
+    assert e.value.status == -1
+
+
+def test_tile_validation(dd):
+    w = fb.LBAND
+    p = dd.Plan(w.nchan, w.fch1, w.foff, w.tsamp, w.dm_list())
+    assert p.get_tiles("u8") == (4, 16, 1, 8)
+    p.set_tiles("u8", 2, 8, 2, 4)
+    assert p.get_tiles("u8") == (2, 8, 2, 4)
+    for bad in [(3, 8, 1, 8), (4, 16, 2, 8), (4, 8, 1, 7), (4, 8, 1, 0), (1, 1, 1, 96),
+                (4, 16, 1, 64)]:   # the last needs more shared memory than a CTA has
+        with pytest.raises(dd.DDError):
+            p.set_tiles("u8", *bad)
+    with pytest.raises(dd.DDError):
+        p.set_tiles("f32", 2, 8, 1, 128)
+
+
+def test_execute_validates_before_touching_a_gpu(dd):
+    """Every layout error is reported as DD_ERR_INVALID by host checks alone."""
+    w = fb.SMALL
+    p = dd.Plan(w.nchan, w.fch1, w.foff, w.tsamp, w.dm_list())
+    S = p.maxshift
+    good = dict(in_ptr=4096, dtype=0, in_pitch=8512, nsamp_in=8192 + S, out_ptr=8192,
+                out_pitch=8192, nsamp_out=8192)
+    bad = [
+        dict(nsamp_in=8192 + S - 1),       # rows too short for maxshift
+        dict(in_pitch=8500),               # pitch not a multiple of 16 bytes
+        dict(out_pitch=8190),              # output pitch not a multiple of 4 floats
+        dict(in_pitch=8000),               # pitch shorter than the row
+        dict(in_ptr=4097),                 # misaligned pointer
+        dict(out_ptr=0),                   # NULL output
+        dict(dtype=7),                     # unknown dtype
+        dict(nsamp_out=-1),
+    ]
+    for b in bad:
+        args = {**good, **b}
+        with pytest.raises(dd.DDError) as e:
+            p.execute_ptr(args["in_ptr"], args["dtype"], args["in_pitch"], args["nsamp_in"],
+                          args["out_ptr"], args["out_pitch"], args["nsamp_out"])
+        assert e.value.status == -1, b
+    # nsamp_out == 0 is a no-op and needs no device
+    p.execute_ptr(0, 0, 16, 0, 0, 0, 0)
+
+
+def test_status_codes_and_messages(dd):
+    with pytest.raises(dd.DDError) as e:
+        dd.Plan(8, 1500.0, -1.0, 0.0, [0.0])
+    assert "tsamp" in str(e.value)
+    assert dd.lib.dd_plan_maxshift(None) == -1

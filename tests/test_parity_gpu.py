@@ -1,0 +1,264 @@
+"""GPU parity of the CUDA path (through the C ABI) against the CPU oracle.
+
+uint8: bit-exact.  FP16/FP32: the same integer-valued noise is exact too (FP32
+sums of integers below 2^24); unquantised ("-frac") data must satisfy
+|gpu - oracle64| <= 1e-6 * sum_c |in[c][t+s(c,d)]| in every checked cell.
+"""
+import numpy as np
+import pytest
+
+import filterbank as fb
+from tests.cases import sample_cells, workload_input
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-6  # relative to sum |in| along the curve
+
+
+@pytest.fixture(scope="module")
+def dd():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1111_6399_gb300 import build
+    build.build()
+    import paper_1111_6399_gb300 as pkg
+    return pkg
+
+
+def _dev(a: np.ndarray):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def _out(ndm, nsamp_out, pad_rows=0, pad_cols=0, fill=np.nan):
+    pitch = (nsamp_out + pad_cols + 3) // 4 * 4
+    return torch.full((ndm + pad_rows, pitch), fill, dtype=torch.float32, device="cuda")
+
+
+def _run(dd, plan, data, nsamp_in, nsamp_out, pad_rows=0, pad_cols=4):
+    x = _dev(data)
+    if data.dtype == np.float16:
+        x = x.view(torch.float16)
+    out = _out(plan.ndm, nsamp_out, pad_rows, pad_cols, fill=-7.0)
+    plan.execute(x, out[:plan.ndm], nsamp_in=nsamp_in, nsamp_out=nsamp_out)
+    plan.sync(torch.cuda.current_stream())
+    got = out.cpu().numpy()
+    # nothing written outside the plane
+    assert np.all(got[:, nsamp_out:] == -7.0)
+    assert np.all(got[plan.ndm:] == -7.0)
+    return got[:plan.ndm, :nsamp_out]
+
+
+def _check_float(got, want, asum):
+    err = np.abs(got.astype(np.float64) - want)
+    bound = TOL * asum
+    assert np.all(err <= bound), float(np.max(err / np.maximum(asum, 1e-30)))
+
+
+def _random_case(rng, nchan, ndm, nsamp_out, kind, dm_hi=80.0, sorted_dms=False):
+    fch1 = float(rng.uniform(300.0, 1500.0))
+    foff = -float(rng.uniform(0.05, min(2.0, 0.8 * fch1 / nchan)))
+    tsamp = float(rng.uniform(6.4e-5, 5e-4))
+    import oracle
+    table = oracle.dmshift(nchan, fch1, foff, tsamp)
+    dms = rng.uniform(0.0, dm_hi, size=ndm).astype(np.float32)
+    if sorted_dms:
+        dms.sort()
+    S = oracle.maxshift(table, dms)
+    nin = nsamp_out + S + int(rng.integers(0, 40))
+    elem = {"u8": 1, "f16": 2, "f32": 4, "f16-frac": 2, "f32-frac": 4}[kind]
+    step = 16 // elem
+    pitch = (nin + step - 1) // step * step + step * int(rng.integers(0, 3))
+    data = fb.random_filterbank(rng, nchan, nin, kind, pitch=pitch)
+    return (fch1, foff, tsamp), table, dms, nin, data
+
+
+# ---------------------------------------------------------------------------
+
+def test_small_workload_bit_exact(dd, oracle_lib):
+    w = fb.SMALL
+    table, dms, S, data = workload_input(w)
+    plan = dd.Plan(w.nchan, w.fch1, w.foff, w.tsamp, dms)
+    got = _run(dd, plan, data, w.nsamp_out + S, w.nsamp_out)
+    want = oracle_lib.dedisperse(np.ascontiguousarray(data[:, :w.nsamp_out + S]), table, dms,
+                                 w.nsamp_out)
+    assert np.array_equal(got, want)
+
+
+TILES_U8 = [(4, 16, 1, 8), (4, 4, 2, 8), (2, 3, 1, 2), (1, 1, 1, 16), (4, 5, 3, 4),
+            (2, 8, 1, 32), (1, 16, 1, 64)]
+
+
+@pytest.mark.parametrize("tiles", TILES_U8)
+@pytest.mark.parametrize("seed", [0, 1])
+def test_u8_fuzz_bit_exact(dd, oracle_lib, tiles, seed):
+    """Ragged nchan/ndm/nsamp (not multiples of any tile), unsorted non-integer
+    DMs, padded pitches, several tile shapes: every cell bit-exact."""
+    rng = np.random.default_rng(1000 * seed + sum(tiles))
+    nchan = int(rng.integers(3, 300))
+    ndm = int(rng.integers(1, 150))
+    nsamp_out = int(rng.integers(1, 5000))
+    band, table, dms, nin, data = _random_case(rng, nchan, ndm, nsamp_out, "u8")
+    plan = dd.Plan(nchan, *band, dms)
+    try:
+        plan.set_tiles("u8", *tiles)
+    except dd.DDError:
+        pytest.skip("tile shape does not fit this band")
+    got = _run(dd, plan, data, nin, nsamp_out)
+    want = oracle_lib.dedisperse(np.ascontiguousarray(data[:, :nin]), table, dms, nsamp_out)
+    assert np.array_equal(got, want)
+
+
+@pytest.mark.parametrize("kind", ["f32", "f16", "f32-frac", "f16-frac"])
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_float_fuzz(dd, oracle_lib, kind, seed):
+    rng = np.random.default_rng(77 + seed)
+    nchan = int(rng.integers(3, 400))
+    ndm = int(rng.integers(1, 80))
+    nsamp_out = int(rng.integers(1, 3000))
+    band, table, dms, nin, data = _random_case(rng, nchan, ndm, nsamp_out, kind)
+    plan = dd.Plan(nchan, *band, dms)
+    if seed == 2:
+        plan.set_tiles(kind[:3], 1, 3, 2, 2)
+    got = _run(dd, plan, data, nin, nsamp_out)
+    want, asum = oracle_lib.dedisperse(np.ascontiguousarray(data[:, :nin]), table, dms,
+                                       nsamp_out, with_abssum=True)
+    if kind.endswith("frac"):
+        _check_float(got, want, asum)
+    else:
+        assert np.array_equal(got.astype(np.float64), want)
+
+
+def test_extreme_values_u8_4096_channels(dd, oracle_lib):
+    """All-255 input over 4096 channels: the largest sums (1,044,480) are exact,
+    including across the 256-channel SWAR widening."""
+    nchan, ndm, nsamp_out = 4096, 8, 2048
+    dms = np.linspace(0, 5, ndm).astype(np.float32)
+    plan = dd.Plan(nchan, 150.0, -0.00732421875, 327.68e-6, dms)
+    nin = nsamp_out + plan.maxshift
+    data = np.full((nchan, (nin + 15) // 16 * 16), 255, dtype=np.uint8)
+    got = _run(dd, plan, data, nin, nsamp_out)
+    assert np.all(got == 4096 * 255)
+
+
+def test_degenerate_shapes(dd, oracle_lib):
+    rng = np.random.default_rng(5)
+    # one channel, one DM, one output sample; all DMs zero; DM list with repeats
+    for nchan, dms, nsamp_out in [(1, [0.0], 1), (1, [7.5], 33), (5, [0.0, 0.0, 0.0], 100),
+                                  (7, [3.0, 1.0, 3.0, 1.0, 2.0], 257), (64, [500.0], 64)]:
+        dms = np.array(dms, np.float32)
+        plan = dd.Plan(nchan, 1400.0, -1.5, 1e-4, dms)
+        nin = nsamp_out + plan.maxshift
+        data = fb.random_filterbank(rng, nchan, nin, "u8", pitch=(nin + 15) // 16 * 16)
+        got = _run(dd, plan, data, nin, nsamp_out)
+        table = oracle_lib.dmshift(nchan, 1400.0, -1.5, 1e-4)
+        want = oracle_lib.dedisperse(np.ascontiguousarray(data[:, :nin]), table, dms, nsamp_out)
+        assert np.array_equal(got, want)
+
+
+def test_zero_samples_is_a_no_op(dd):
+    plan = dd.Plan(8, 1400.0, -1.0, 1e-4, [0.0, 1.0])
+    out = torch.full((2, 16), 3.0, device="cuda")
+    x = torch.zeros((8, 64), dtype=torch.uint8, device="cuda")
+    plan.execute(x, out, nsamp_out=0)
+    plan.sync()
+    assert torch.all(out == 3.0)
+
+
+def test_execute_host_matches_device_path(dd, oracle_lib):
+    """The host-buffer form (blocked, overlap tails copied on the device) gives
+    the same plane as the device form, on pinned and pageable buffers."""
+    w = fb.SMALL
+    rng = np.random.default_rng(8)
+    dms = np.arange(0, 300, dtype=np.float32)
+    plan = dd.Plan(w.nchan, w.fch1, w.foff, w.tsamp, dms)
+    nsamp_out = 150_000  # several 65536-sample blocks and a ragged last block
+    nin = nsamp_out + plan.maxshift
+    data = fb.random_filterbank(rng, w.nchan, nin, "u8")
+    dev = _run(dd, plan, np.pad(data, ((0, 0), (0, (-nin) % 16))), nin, nsamp_out)
+    out = np.full((len(dms), nsamp_out), -1.0, np.float32)
+    plan.execute_host(data, out)
+    assert np.array_equal(out, dev)
+    pinned_in = torch.from_numpy(data).pin_memory()
+    pinned_out = torch.empty((len(dms), nsamp_out), dtype=torch.float32).pin_memory()
+    plan.execute_host(pinned_in, pinned_out)
+    assert np.array_equal(pinned_out.numpy(), dev)
+    d_idx, t_idx = sample_cells(rng, len(dms), nsamp_out, 500)
+    table = oracle_lib.dmshift(w.nchan, w.fch1, w.foff, w.tsamp)
+    want, _ = oracle_lib.dedisperse_cells(data, table, dms, d_idx, t_idx)
+    assert np.array_equal(out[d_idx, t_idx].astype(np.float64), want)
+
+
+def test_lband_full_size_sampled_cells(dd, oracle_lib):
+    """The 1024-channel L-band beam at full size, default tiles (the benchmarked
+    launch): sampled cells bit-exact, DM-0 row equal to the channel sum, and
+    each injected pulse recovered at its DM."""
+    w = fb.LBAND
+    table, dms, S, data = workload_input(w)
+    plan = dd.Plan(w.nchan, w.fch1, w.foff, w.tsamp, dms)
+    got = _run(dd, plan, data, w.nsamp_out + S, w.nsamp_out)
+    rng = np.random.default_rng(2)
+    d_idx, t_idx = sample_cells(rng, w.ndm, w.nsamp_out, 3000)
+    want, _ = oracle_lib.dedisperse_cells(data, table, dms, d_idx, t_idx)
+    assert np.array_equal(got[d_idx, t_idx].astype(np.float64), want)
+    chan_sum = data[:, :w.nsamp_out].sum(axis=0, dtype=np.int64)
+    assert np.array_equal(got[0], chan_sum.astype(np.float32))
+    for p in fb.all_pulses(w):
+        d = int(np.where(dms == np.float32(p.dm))[0][0])
+        win = got[d, p.t:p.t + p.width]
+        assert win.mean() > got[d].mean() + 0.8 * w.nchan * p.amp
+
+
+@pytest.mark.parametrize("kind", ["u8", "f16", "f32"])
+def test_lowfreq_full_size_sampled_cells(dd, oracle_lib, kind):
+    """The 4096-channel low-frequency beam at full size (2000 DMs, 262144
+    samples) in each storage type: the same integer-valued noise, so every
+    sampled cell is exact."""
+    w = fb.LOWFREQ
+    table, dms, S, data = _lowfreq_input(kind)
+    plan = dd.Plan(w.nchan, w.fch1, w.foff, w.tsamp, dms)
+    got = _run(dd, plan, data, w.nsamp_out + S, w.nsamp_out)
+    rng = np.random.default_rng(3)
+    d_idx, t_idx = sample_cells(rng, w.ndm, w.nsamp_out, 1500)
+    want, _ = oracle_lib.dedisperse_cells(data, table, dms, d_idx, t_idx)
+    assert np.array_equal(got[d_idx, t_idx].astype(np.float64), want)
+    for p in fb.all_pulses(w):
+        d = int(np.argmin(np.abs(dms - np.float32(p.dm))))
+        assert got[d, p.t:p.t + p.width].mean() > got[d].mean() + 0.8 * w.nchan * p.amp
+
+
+_LOWFREQ_CACHE = {}
+
+
+def _lowfreq_input(kind):
+    if "u8" not in _LOWFREQ_CACHE:
+        _LOWFREQ_CACHE.clear()
+        _LOWFREQ_CACHE["u8"] = workload_input(fb.LOWFREQ, "u8")
+    table, dms, S, data = _LOWFREQ_CACHE["u8"]
+    if kind == "u8":
+        return table, dms, S, data
+    return table, dms, S, data.astype(np.float16 if kind == "f16" else np.float32)
+
+
+@pytest.mark.parametrize("kind", ["f16-frac", "f32-frac"])
+def test_lowfreq_band_noninteger_within_tolerance(dd, oracle_lib, kind):
+    """Unquantised noise on the 4096-channel band (2000 DMs; shorter time axis):
+    every sampled cell within 1e-6 of sum |in| along its curve."""
+    w = fb.LOWFREQ
+    table, dms, S, data = workload_input(w, kind, nsamp_out=8192)
+    plan = dd.Plan(w.nchan, w.fch1, w.foff, w.tsamp, dms)
+    got = _run(dd, plan, data, 8192 + S, 8192)
+    rng = np.random.default_rng(4)
+    d_idx, t_idx = sample_cells(rng, w.ndm, 8192, 20000)
+    want, asum = oracle_lib.dedisperse_cells(data, table, dms, d_idx, t_idx)
+    _check_float(got[d_idx, t_idx], want, asum)
+
+
+def test_launch_count_and_status(dd):
+    n0 = dd.launch_count()
+    plan = dd.Plan(16, 1400.0, -1.0, 1e-4, [0.0, 2.0])
+    x = torch.zeros((16, 1024), dtype=torch.uint8, device="cuda")
+    out = torch.empty((2, 512), device="cuda")
+    plan.execute(x, out)
+    plan.sync()
+    assert dd.launch_count() == n0 + 1
