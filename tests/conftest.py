@@ -18,3 +18,12 @@ def oracle_lib():
     import oracle
     oracle.build()
     return oracle
+
+
+@pytest.fixture(scope="session")
+def built_lib():
+    """Build libdd.so (by path, before the package is imported) and return the package."""
+    import __graft_entry__
+    __graft_entry__._build_module().build()
+    import paper_1111_6399_gb300
+    return paper_1111_6399_gb300

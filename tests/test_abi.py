@@ -13,11 +13,8 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
 @pytest.fixture(scope="module")
-def dd():
-    from paper_1111_6399_gb300 import build
-    build.build()
-    import paper_1111_6399_gb300 as pkg
-    return pkg
+def dd(request):
+    return request.getfixturevalue("built_lib")
 
 
 def _declared():

@@ -17,13 +17,10 @@ TOL = 1e-6  # relative to sum |in| along the curve
 
 
 @pytest.fixture(scope="module")
-def dd():
+def dd(request):
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
-    from paper_1111_6399_gb300 import build
-    build.build()
-    import paper_1111_6399_gb300 as pkg
-    return pkg
+    return request.getfixturevalue("built_lib")
 
 
 def _dev(a: np.ndarray):
