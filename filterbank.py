@@ -148,13 +148,15 @@ def filterbank(nchan: int, nsamp_in: int, seed: int, pulses=(), delays=(),
 
 def random_filterbank(rng: np.random.Generator, nchan: int, nsamp: int, kind: str = "u8",
                       pitch: int | None = None) -> np.ndarray:
-    """Unstructured random rows for fuzz cases (full uint8 range, or floats)."""
+    """Unstructured random rows for fuzz cases: the full uint8 range ("u8", and
+    the same integers stored as "f16"/"f32"), or non-integer uniform values in
+    [0, 255) rounded to the storage type ("f16-frac"/"f32-frac")."""
     pitch = nsamp if pitch is None else pitch
-    if kind == "u8":
-        out = np.zeros((nchan, pitch), dtype=np.uint8)
-        out[:, :nsamp] = rng.integers(0, 256, size=(nchan, nsamp), dtype=np.uint8)
-    else:
-        dt = np.float16 if kind.startswith("f16") else np.float32
-        out = np.zeros((nchan, pitch), dtype=dt)
+    dt = {"u8": np.uint8, "f16": np.float16, "f32": np.float32,
+          "f16-frac": np.float16, "f32-frac": np.float32}[kind]
+    out = np.zeros((nchan, pitch), dtype=dt)
+    if kind.endswith("-frac"):
         out[:, :nsamp] = rng.uniform(0.0, 255.0, size=(nchan, nsamp)).astype(dt)
+    else:
+        out[:, :nsamp] = rng.integers(0, 256, size=(nchan, nsamp), dtype=np.uint8).astype(dt)
     return out

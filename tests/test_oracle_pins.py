@@ -256,7 +256,7 @@ def test_float_paths_sum_in_fp64_exactly(oracle_lib):
     partial sum is exact, so each cell equals math.fsum of its curve, and the
     absolute-sum plane equals fsum of |in|."""
     rng = np.random.default_rng(9)
-    for kind in ("f32", "f16"):
+    for kind in ("f32", "f16", "f32-frac", "f16-frac"):
         data, table, dms = _tiny_case(rng, 64, 6, 100, kind)
         out, asum = oracle_lib.dedisperse(data, table, dms, 100, with_abssum=True)
         for d in range(len(dms)):
