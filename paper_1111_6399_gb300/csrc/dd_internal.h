@@ -63,6 +63,7 @@ struct dd_plan_s {
     std::vector<int> order;        // sorted position -> caller index
     std::vector<float> dm_sorted;  // [ndm] ascending
     dd_tiles tiles[3]{};
+    bool tiles_auto[3] = {true, true, true};  // resolved by the plan until set
     std::mutex mu;
     std::map<int, dd::DevTables> dev;      // per CUDA device
     std::map<uint64_t, dd::Geometry> geo;  // per (dtype, tiles) key
@@ -73,8 +74,13 @@ namespace dd {
 // Thread-local error message; returns st for chaining.
 dd_status fail(dd_status st, const std::string &msg);
 
-// Default tile shape for a dtype.
+// Preferred tile shape for a dtype.
 dd_tiles default_tiles(dd_dtype t);
+
+// Tile shapes tried, in order, when the plan picks one itself: the preferred
+// shape, then fewer channels per stage, then fewer DMs per CTA (more time
+// warps), down to one DM per CTA, which always fits.
+std::vector<dd_tiles> auto_tiles(dd_dtype t);
 
 // Validate a tile shape for dtype and compute the launch geometry for the
 // plan (shared-memory window bound over every DM tile and channel).

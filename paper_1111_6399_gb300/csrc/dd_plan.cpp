@@ -58,6 +58,20 @@ dd_tiles default_tiles(dd_dtype t) {
     }
 }
 
+std::vector<dd_tiles> auto_tiles(dd_dtype t) {
+    const dd_tiles base = default_tiles(t);
+    const int max_t_cta = 4096;  // samples per CTA along time
+    std::vector<dd_tiles> out;
+    for (int dcta = base.dm_per_thread * base.dm_warps; dcta >= 1; dcta /= 2) {
+        const int dthr = std::min(base.dm_per_thread, dcta);
+        const int wd = dcta / dthr;
+        const int wt = std::max(1, std::min(16 / wd, max_t_cta / warp_span(t)));
+        for (int cs = base.chan_per_stage; cs >= 2; cs /= 2)
+            out.push_back(dd_tiles{dthr, wd, wt, cs});
+    }
+    return out;
+}
+
 dd_status make_geometry(dd_plan_s *p, dd_dtype t, const dd_tiles &tl, Geometry *g) {
     if (!valid_dtype(t))
         return fail(DD_ERR_INVALID, "unknown dtype");
@@ -121,7 +135,19 @@ dd_status plan_geometry(dd_plan_s *p, dd_dtype t, Geometry *g) {
         return DD_OK;
     }
     Geometry r;
-    dd_status st = make_geometry(p, t, p->tiles[t], &r);
+    dd_status st = DD_ERR_INVALID;
+    if (p->tiles_auto[t]) {
+        for (const dd_tiles &cand : auto_tiles(t)) {
+            if ((st = make_geometry(p, t, cand, &r)) == DD_OK) {
+                p->tiles[t] = cand;
+                break;
+            }
+        }
+        p->tiles_auto[t] = false;
+        key = geo_key(t, p->tiles[t]);
+    } else {
+        st = make_geometry(p, t, p->tiles[t], &r);
+    }
     if (st != DD_OK)
         return st;
     p->geo[key] = r;
@@ -268,6 +294,10 @@ dd_status dd_plan_dmshift(dd_plan_t p, float *host_out) {
 dd_status dd_plan_get_tiles(dd_plan_t p, dd_dtype t, dd_tiles *out) {
     if (!p || !out || !valid_dtype(t))
         return dd::fail(DD_ERR_INVALID, "NULL argument or unknown dtype");
+    dd::Geometry g;
+    dd_status st = dd::plan_geometry(p, t, &g);  // resolves an automatic choice
+    if (st != DD_OK)
+        return st;
     std::lock_guard<std::mutex> lk(p->mu);
     *out = p->tiles[t];
     return DD_OK;
@@ -282,6 +312,7 @@ dd_status dd_plan_set_tiles(dd_plan_t p, dd_dtype t, const dd_tiles *tl) {
         return st;
     std::lock_guard<std::mutex> lk(p->mu);
     p->tiles[t] = *tl;
+    p->tiles_auto[t] = false;
     return DD_OK;
 }
 
