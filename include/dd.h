@@ -72,7 +72,8 @@ typedef struct dd_plan_s *dd_plan_t;
 /* Tile shape of the de-dispersion kernel (chosen by the plan or the autotuner).
  *   dm_per_thread    trial DMs each thread accumulates (register accumulators)
  *   dm_warps         warps of a CTA along the DM axis
- *   time_warps       warps of a CTA along the time axis
+ *   time_warps       warps of a CTA along the time axis (dm_warps*time_warps <= 12;
+ *                    the CTA has one more warp that stages the data)
  *   chan_per_stage   channels staged in shared memory per pipeline stage
  * A CTA covers dm_per_thread*dm_warps DMs and time_warps*span samples, where
  * span = 1024 (uint8), 512 (FP16) or 256 (FP32) samples per warp. */

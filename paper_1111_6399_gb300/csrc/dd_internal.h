@@ -26,6 +26,9 @@ constexpr int kSwarChannels = 256;
 constexpr int kFloatBlock = 64;
 
 constexpr int kMaxSmem = 232448;  // 227 KB dynamic shared memory per CTA
+// Consumer warps per CTA (plus one producer warp).  13 warps put at most 4
+// on each SM sub-partition, which leaves 128 registers per thread.
+constexpr int kMaxConsumerWarps = 12;
 
 // Device status word values (written by kernels, read by dd_sync).
 constexpr int kDevOk = 0;
@@ -38,6 +41,11 @@ struct DevTables {
     int *perm = nullptr;         // [ndm_pad]: output row of sorted DM k, -1 for padding
     int *status = nullptr;       // device status word
     int ndm_pad = 0;
+    // Phase-plane scratch of dd_execute (grown on demand).  Uses on different
+    // streams are ordered by scratch_done: each use waits for the previous one.
+    void *scratch = nullptr;
+    size_t scratch_bytes = 0;
+    void *scratch_done = nullptr;  // cudaEvent_t
 };
 
 // Launch geometry derived from a tile shape and the plan's tables.
@@ -48,8 +56,10 @@ struct Geometry {
     int t_cta = 0;        // samples per CTA
     int ntile_d = 0;      // DM tiles
     int wp = 0;           // bytes of one phase row in shared memory
+    int nstages = 0;      // shared-memory stages in the copy ring
+    int zero_bytes = 0;   // zero row read by padding channels
     int smem = 0;         // dynamic shared memory per CTA
-    int threads = 0;
+    int threads = 0;      // consumer warps + one producer warp
 };
 
 }  // namespace dd
@@ -92,10 +102,20 @@ dd_status plan_geometry(dd_plan_s *p, dd_dtype t, Geometry *g);
 // Device tables for the current device, uploaded on first use.
 dd_status device_tables(dd_plan_s *p, DevTables **out);
 
-// Launch the de-dispersion kernel (dd_kernel.cu).
+// Bytes of phase-plane scratch for one input (0 for FP32).
+int64_t scratch_bytes(dd_dtype dtype, int nchan, int64_t in_pitch_b);
+
+// Launch the phase-plane pre-pass (8/16-bit input) and the de-dispersion
+// kernel (dd_kernel.cu) on stream, with caller-provided scratch.
 dd_status launch_dedisperse(dd_plan_s *p, const Geometry &g, const DevTables &dt,
                             const void *in, dd_dtype dtype, int64_t in_pitch, int64_t nsamp_in,
-                            float *out, int64_t out_pitch, int64_t nsamp_out, void *stream);
+                            float *out, int64_t out_pitch, int64_t nsamp_out, void *scratch,
+                            void *stream);
+
+// launch_dedisperse with the plan's own per-device scratch (dd_exec.cpp).
+dd_status run_with_plan_scratch(dd_plan_s *p, const Geometry &g, DevTables &dt, const void *in,
+                                dd_dtype dtype, int64_t in_pitch, int64_t nsamp_in, float *out,
+                                int64_t out_pitch, int64_t nsamp_out, void *stream);
 
 void count_launch(int n = 1);
 

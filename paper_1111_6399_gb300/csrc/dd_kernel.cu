@@ -2,36 +2,40 @@
 //
 //   out[d][t] = sum_c in[c][t + s(c,d)],   s(c,d) = trunc(dm[d] * dmshift[c])
 //
-// Design (Sec. 3 of the paper gives the three rules; this is how they map to
-// a Blackwell SM):
-//  * Accumulators in registers.  A thread owns dm_per_thread trial DMs x 8
-//    four-byte words of output time (32 samples for uint8, lane-interleaved so
-//    that a warp's shared-memory reads hit 32 consecutive banks).  A CTA owns a
-//    rectangle of (DM,t), as in Fig. 2.
-//  * The (f,t) data staged next to the SMs.  Per pipeline stage one thread
-//    issues one TMA bulk copy (cp.async.bulk, no multicast) per channel row:
-//    the 16-byte aligned window [t0 + s(c,dm_min), t0 + T + s(c,dm_max)) of
-//    that channel, completing on an mbarrier.  Two stages alternate, so the
-//    copy of stage i+1 runs while stage i is summed.  Shifts are arbitrary in
-//    bytes, so for 8/16-bit data the stage also holds the window re-aligned
-//    by 1..3 bytes (uint8) or 2 bytes (FP16): every shifted 4-byte read is then
-//    an aligned, conflict-free LDS.32.
-//  * Little shift arithmetic.  One FP32 multiply and one truncation per
-//    (channel, DM) per thread, reused for 8 words (32 uint8 samples).
+// Sec. 3 of the paper sets three rules: accumulators in the fastest memory,
+// the right (f,t) data always next to the SMs, and few operations for the
+// shift.  Their sm_103a form here:
+//
+//  * Accumulators in registers.  A consumer thread owns dm_per_thread trial
+//    DMs x 8 four-byte words of output time (32 uint8 samples), lane-interleaved
+//    so each shared-memory read of a warp covers 32 consecutive banks.  A CTA
+//    owns a rectangle of (DM,t) (Fig. 2).
+//  * Data next to the SMs.  A producer warp stages each channel's window
+//    [t0 + s(c,dm_min), t0 + T + s(c,dm_max)) with TMA bulk copies (no
+//    multicast) into a ring of shared-memory stages handed over through
+//    full/empty mbarriers, so copies run ahead of the arithmetic and no
+//    CTA-wide barrier sits in the loop.  Shifts are arbitrary in bytes while
+//    shared-memory words are 4-byte aligned, so for 8/16-bit data the window
+//    is staged once per byte phase (1..3 or 2 bytes later), fetched from phase
+//    planes that a pre-pass writes to global scratch; every shifted read is
+//    then an aligned, conflict-free LDS.32.
+//  * Shift arithmetic.  One FP32 multiply and one truncation per (channel,
+//    DM) per thread, reused for 8 words.
 //  * uint8 sums use 16-bit SWAR lanes: for a word x of 4 samples, L1 += x and
 //    L2 += (x >> 8) & 0x00ff00ff.  After at most 256 channels
 //    L2 = {sum b1, sum b3} and L1 - 256*L2 = {sum b0, sum b2} exactly; these are
-//    widened into the FP32 output (exact: every sum < 2^24).  IADD3 folds two
-//    channels into one instruction, so a word of 4 samples x 2 channels costs
-//    2 LDS + 2 PRMT + 2 IADD3.
+//    widened into the FP32 output (exact: every sum < 2^24).  Per word and two
+//    channels: 2 LDS + 1 IADD3 (ALU) + 2 PRMT (ALU) + 2 IMAD (FMA pipe), which
+//    balances the integer ALU and FMA pipes.
 //  * FP16/FP32 sums: FP32 partials over blocks of 64 channels, combined into a
 //    running sum with TwoSum compensation (error ~1e-7 of sum |in|).
 //
-// Every wait on an mbarrier is bounded by the global timer; a wait that runs
-// out records a timeout in the status word and the CTA leaves after a second
-// bounded wait for its own copies.
+// Every mbarrier wait is bounded by the global timer; a wait that runs out
+// records a timeout in the status word and the thread leaves (the producer
+// first waits, again bounded, for the copies it issued).
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdint>
 
 #include "dd_internal.h"
@@ -43,28 +47,32 @@ constexpr uint64_t kWaitLimitNs = 2000000000ull;  // 2 s
 
 struct KArgs {
     const uint8_t *in;
-    int64_t in_pitch_b;    // bytes between channel rows
-    int64_t nsamp_in;      // valid samples per row
+    const uint8_t *planes;  // byte-phase planes 1..NPH-1 (NULL for FP32)
+    int64_t plane_stride;   // bytes between planes
+    int64_t in_pitch_b;     // bytes between channel rows
+    int64_t nsamp_in;       // valid samples per row
     float *out;
-    int64_t out_pitch;     // floats between DM rows
+    int64_t out_pitch;      // floats between DM rows
     int64_t nsamp_out;
     const float *dmshift;
     const float *dm_sorted;
     const int *perm;
     int nchan;
-    int ndm_pad;
     int dm_warps;
+    int time_warps;
     int ntile_d;
     int cstage;
-    int wp;                // bytes per phase row
+    int nstages;
+    int wp;                 // bytes per phase row
+    int zero_bytes;         // bytes of the zero row (padding channels)
+    uint32_t one;           // the constant 1, opaque to the compiler
     int *status;
 };
 
 struct __align__(16) RowMeta {
     int base;     // smem byte offset of window sample t0 (may precede the row)
     float ds;     // dmshift of the channel (0 for padding rows)
-    int bytes;    // bytes fetched into phase 0 (0: padding row, zero filled)
-    int pad;
+    int pad0, pad1;
 };
 
 __device__ __forceinline__ uint32_t smem_addr(const void *p) {
@@ -86,6 +94,10 @@ __device__ __forceinline__ void mbar_expect_tx_arrive(uint32_t mb, uint32_t byte
                  : "memory");
 }
 
+__device__ __forceinline__ void mbar_arrive(uint32_t mb) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(mb) : "memory");
+}
+
 __device__ __forceinline__ bool mbar_try(uint32_t mb, uint32_t parity) {
     uint32_t ok;
     asm volatile(
@@ -97,16 +109,18 @@ __device__ __forceinline__ bool mbar_try(uint32_t mb, uint32_t parity) {
     return ok != 0;
 }
 
-// Bounded wait; false if the limit ran out.
-__device__ bool mbar_wait(uint32_t mb, uint32_t parity) {
-    if (mbar_try(mb, parity))
-        return true;
+// Bounded wait for the completion of the phase with the given parity.
+__device__ __noinline__ bool mbar_wait_slow(uint32_t mb, uint32_t parity) {
     const uint64_t t0 = global_ns();
     while (!mbar_try(mb, parity)) {
         if (global_ns() - t0 > kWaitLimitNs)
             return false;
     }
     return true;
+}
+
+__device__ __forceinline__ bool mbar_wait(uint32_t mb, uint32_t parity) {
+    return mbar_try(mb, parity) || mbar_wait_slow(mb, parity);
 }
 
 __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t bytes,
@@ -124,8 +138,11 @@ __device__ __forceinline__ uint32_t prmt(uint32_t a, uint32_t b, uint32_t sel) {
     return r;
 }
 
-__device__ __forceinline__ uint32_t iadd3(uint32_t a, uint32_t b, uint32_t c) {
-    return a + b + c;
+// acc + p on the FMA pipe (p * one + acc with one == 1 at run time).
+__device__ __forceinline__ uint32_t imad_acc(uint32_t p, uint32_t one, uint32_t acc) {
+    uint32_t r;
+    asm("mad.lo.u32 %0, %1, %2, %3;" : "=r"(r) : "r"(p), "r"(one), "r"(acc));
+    return r;
 }
 
 __device__ __forceinline__ int shift_of(float dm, float ds) {
@@ -152,19 +169,20 @@ __device__ __forceinline__ void record(int *status, int code) {
     atomicCAS(status, kDevOk, code);
 }
 
-// ---------------------------------------------------------------------------
-// Output stores.  Word k of lane L covers samples t = tw + (4/ELEM)*(L + 32k) ...
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ void store4(float *row, int64_t t, int64_t n, float4 v, bool accumulate) {
+__device__ __forceinline__ void store4(float *row, int64_t t, int64_t n, float4 v,
+                                       bool accumulate) {
     if (t + 3 < n) {
         float4 *p = reinterpret_cast<float4 *>(row + t);
         if (accumulate) {
-            float4 o = *p;
-            v.x += o.x; v.y += o.y; v.z += o.z; v.w += o.w;
+            const float4 o = *p;
+            v.x += o.x;
+            v.y += o.y;
+            v.z += o.z;
+            v.w += o.w;
         }
         *p = v;
     } else {
-        float e[4] = {v.x, v.y, v.z, v.w};
+        const float e[4] = {v.x, v.y, v.z, v.w};
         for (int i = 0; i < 4; ++i)
             if (t + i < n)
                 row[t + i] = accumulate ? row[t + i] + e[i] : e[i];
@@ -172,118 +190,184 @@ __device__ __forceinline__ void store4(float *row, int64_t t, int64_t n, float4 
 }
 
 // ---------------------------------------------------------------------------
-// The kernel.  ELEM = bytes per sample (1, 2, 4); DT = DMs per thread.
+// Pre-pass: byte-phase planes.  Plane p (1 <= p < NPH) holds every input row
+// advanced by p bytes (uint8) or by one sample (FP16): plane byte j of row c
+// is input byte j + p*ELEM of row c.
+// ---------------------------------------------------------------------------
+template <int ELEM>
+__global__ void __launch_bounds__(256) phase_planes_kernel(const uint8_t *__restrict__ in,
+                                                           int64_t pitch_b, int nchan,
+                                                           int64_t groups_per_row,
+                                                           uint8_t *__restrict__ planes,
+                                                           int64_t plane_stride) {
+    constexpr int NPH = 4 / ELEM;
+    const int64_t total = groups_per_row * nchan;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t c = i / groups_per_row;
+        const int64_t g = i - c * groups_per_row;
+        const uint8_t *row = in + c * pitch_b + 16 * g;
+        const uint4 v = *reinterpret_cast<const uint4 *>(row);
+        const uint32_t nx =
+            (16 * g + 16 < pitch_b) ? *reinterpret_cast<const uint32_t *>(row + 16) : 0u;
+#pragma unroll
+        for (int p = 1; p < NPH; ++p) {
+            const uint32_t sel = (ELEM == 1) ? (0x3210u + 0x1111u * (uint32_t)p) : 0x5432u;
+            uint4 o;
+            o.x = prmt(v.x, v.y, sel);
+            o.y = prmt(v.y, v.z, sel);
+            o.z = prmt(v.z, v.w, sel);
+            o.w = prmt(v.w, nx, sel);
+            *reinterpret_cast<uint4 *>(planes + (p - 1) * plane_stride + c * pitch_b + 16 * g) = o;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// The de-dispersion kernel.  ELEM = bytes per sample (1, 2, 4); DT = DMs per
+// consumer thread.  Warps 0..ncw-1 consume, warp ncw produces.
 // ---------------------------------------------------------------------------
 template <int ELEM, int DT>
-__global__ void __launch_bounds__(512, 1) dedisperse_kernel(const KArgs a) {
-    constexpr int NPH = 4 / ELEM;              // phase copies per row
-    constexpr int SPW = 4 / ELEM;              // samples per 4-byte word
-    constexpr int SPAN = 32 * kWords * SPW;    // samples per warp
+__global__ void __launch_bounds__(32 * (kMaxConsumerWarps + 1), 1) dedisperse_kernel(const KArgs a) {
+    constexpr int NPH = 4 / ELEM;            // phase copies per row
+    constexpr int SPW = 4 / ELEM;            // samples per 4-byte word
+    constexpr int SPAN = 32 * kWords * SPW;  // samples per warp
     constexpr int FLUSH = (ELEM == 1) ? kSwarChannels : kFloatBlock;
 
     extern __shared__ __align__(128) uint8_t smem[];
     const int tid = threadIdx.x;
-    const int nthreads = blockDim.x;
     const int lane = tid & 31;
     const int warp = tid >> 5;
-    const int wdi = warp % a.dm_warps;
-    const int wti = warp / a.dm_warps;
-    const int time_warps = nthreads / 32 / a.dm_warps;
+    const int ncw = a.dm_warps * a.time_warps;  // consumer warps
     const int dm_cta = DT * a.dm_warps;
-    const int t_cta = SPAN * time_warps;
+    const int t_cta = SPAN * a.time_warps;
     const int td = blockIdx.x % a.ntile_d;
     const int64_t t0 = (int64_t)(blockIdx.x / a.ntile_d) * t_cta;
 
     const int cstage = a.cstage;
+    const int nst = a.nstages;
     const int wp = a.wp;
     const int row_bytes = NPH * wp;
     const int stage_bytes = cstage * row_bytes;
-    RowMeta *meta = reinterpret_cast<RowMeta *>(smem + 2 * stage_bytes);
-    uint64_t *mbar = reinterpret_cast<uint64_t *>(smem + 2 * stage_bytes + 2 * cstage * 16);
-    const uint32_t mb0 = smem_addr(&mbar[0]);
+    RowMeta *meta = reinterpret_cast<RowMeta *>(smem + nst * stage_bytes);
+    uint8_t *zero = smem + nst * stage_bytes + nst * cstage * 16;
+    uint64_t *mbar = reinterpret_cast<uint64_t *>(zero + a.zero_bytes);
+    const uint32_t full0 = smem_addr(&mbar[0]);
+    const uint32_t empty0 = smem_addr(&mbar[nst]);
+    const int zero_off = (int)(zero - smem);
 
-    // DM range of this CTA (sorted list) and this thread's DMs.
     const int kcta = td * dm_cta;
-    const float dm_min = a.dm_sorted[kcta];
-    const float dm_max = a.dm_sorted[kcta + dm_cta - 1];
+    const int nstage = (a.nchan + cstage - 1) / cstage;
+
+    for (int i = tid; i < a.zero_bytes / 16; i += blockDim.x)
+        reinterpret_cast<uint4 *>(zero)[i] = make_uint4(0, 0, 0, 0);
+    if (tid == 0) {
+        for (int b = 0; b < nst; ++b) {
+            mbar_init(full0 + 8 * b, 1);
+            mbar_init(empty0 + 8 * b, ncw);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+
+    if (warp == ncw) {
+        // ------------------------------ producer ------------------------------
+        const float dm_min = a.dm_sorted[kcta];
+        const float dm_max = a.dm_sorted[kcta + dm_cta - 1];
+        int issued = 0;
+        bool ok = true;
+        for (int st = 0; st < nstage; ++st) {
+            const int b = st % nst;
+            const int n = st / nst;
+            if (n > 0 && !mbar_wait(empty0 + 8 * b, (n - 1) & 1)) {
+                ok = false;
+                break;
+            }
+            RowMeta *m = meta + b * cstage;
+            uint8_t *buf = smem + b * stage_bytes;
+            uint32_t my_bytes[2] = {0u, 0u};
+            int64_t my_first[2] = {0, 0};
+            bool bad = false;
+            for (int h = 0; h < 2; ++h) {
+                const int r = lane + 32 * h;
+                if (r >= cstage)
+                    break;
+                const int c = st * cstage + r;
+                RowMeta rm;
+                rm.pad0 = rm.pad1 = 0;
+                rm.base = zero_off;
+                rm.ds = 0.0f;
+                if (c < a.nchan) {
+                    const float ds = a.dmshift[c];
+                    const int64_t smin = shift_of(dm_min, ds);
+                    const int64_t smax = shift_of(dm_max, ds);
+                    const int64_t first = (t0 + smin) & ~(int64_t)(16 / ELEM - 1);
+                    int64_t end = t0 + t_cta + smax;
+                    if (end > a.nsamp_in)
+                        end = a.nsamp_in;
+                    const int64_t bytes = ((end - first) * ELEM + 15) & ~(int64_t)15;
+                    if (bytes > wp - 16 || bytes <= 0) {  // excluded by the host checks
+                        bad = true;
+                    } else {
+                        rm.base = (int)(buf + r * row_bytes - smem) + (int)(ELEM * (t0 - first));
+                        rm.ds = ds;
+                        my_bytes[h] = (uint32_t)bytes;
+                        my_first[h] = first;
+                    }
+                }
+                m[r] = rm;
+            }
+            if (bad)
+                record(a.status, kDevCheck);
+            uint32_t total = (my_bytes[0] + my_bytes[1]) * NPH;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1)
+                total += __shfl_xor_sync(0xffffffffu, total, o);
+            __syncwarp();
+            if (lane == 0)
+                mbar_expect_tx_arrive(full0 + 8 * b, total);
+            __syncwarp();
+            for (int h = 0; h < 2; ++h) {
+                const int r = lane + 32 * h;
+                if (r >= cstage || my_bytes[h] == 0)
+                    continue;
+                const int c = st * cstage + r;
+                const int64_t off = (int64_t)c * a.in_pitch_b + my_first[h] * ELEM;
+                const uint32_t dst = smem_addr(buf + r * row_bytes);
+                bulk_g2s(dst, a.in + off, my_bytes[h], full0 + 8 * b);
+#pragma unroll
+                for (int p = 1; p < NPH; ++p)
+                    bulk_g2s(dst + p * wp, a.planes + (p - 1) * a.plane_stride + off, my_bytes[h],
+                             full0 + 8 * b);
+            }
+            issued = st + 1;
+        }
+        if (!ok)
+            record(a.status, kDevTimeout);
+        // Leave only once the last stages issued have landed (and, normally,
+        // been released by the consumers); bounded.
+        for (int st = (issued > nst ? issued - nst : 0); st < issued; ++st) {
+            const int b = st % nst;
+            if (!mbar_wait(ok ? empty0 + 8 * b : full0 + 8 * b, (st / nst) & 1)) {
+                record(a.status, kDevTimeout);
+                break;
+            }
+        }
+        return;
+    }
+
+    // ------------------------------- consumers --------------------------------
+    const int wdi = warp % a.dm_warps;
+    const int wti = warp / a.dm_warps;
     const int kthr = kcta + wdi * DT;
     float dm[DT];
 #pragma unroll
     for (int j = 0; j < DT; ++j)
         dm[j] = a.dm_sorted[kthr + j];
     const int thr_off = ELEM * (wti * SPAN) + 4 * lane;
+    const uint32_t one = a.one;
 
-    if (tid == 0) {
-        mbar_init(mb0, 1);
-        mbar_init(mb0 + 8, 1);
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
-    __syncthreads();
-
-    const int nstage = (a.nchan + cstage - 1) / cstage;
-
-    // Window of channel c fetched by this CTA: [first, first + bytes/ELEM).
-    auto window = [&](int c, int64_t *first, int64_t *bytes) {
-        const float ds = a.dmshift[c];
-        const int64_t smin = shift_of(dm_min, ds);
-        const int64_t smax = shift_of(dm_max, ds);
-        *first = (t0 + smin) & ~(int64_t)(16 / ELEM - 1);
-        int64_t end = t0 + t_cta + smax;
-        if (end > a.nsamp_in)
-            end = a.nsamp_in;
-        *bytes = ((end - *first) * ELEM + 15) & ~(int64_t)15;
-    };
-
-    // Producer: row metadata + one bulk copy per channel row of stage st into
-    // buffer b, all completing on that buffer's mbarrier.
-    auto issue = [&](int st, int b) {
-        RowMeta *m = meta + b * cstage;
-        uint8_t *buf = smem + b * stage_bytes;
-        uint32_t total = 0;
-        bool bad = false;
-        for (int r = 0; r < cstage; ++r) {
-            const int c = st * cstage + r;
-            const int rowstart = (int)(buf + r * row_bytes - smem);
-            RowMeta rm;
-            rm.pad = 0;
-            if (c < a.nchan) {
-                int64_t first, bytes;
-                window(c, &first, &bytes);
-                if (bytes > wp - 16) {  // excluded by the host geometry
-                    bad = true;
-                    bytes = 0;
-                }
-                rm.base = rowstart + (int)(ELEM * (t0 - first));
-                rm.ds = a.dmshift[c];
-                rm.bytes = (int)bytes;
-            } else {
-                rm.base = rowstart;
-                rm.ds = 0.0f;
-                rm.bytes = 0;
-            }
-            m[r] = rm;
-            total += (uint32_t)rm.bytes;
-        }
-        if (bad)
-            record(a.status, kDevCheck);
-        const uint32_t mb = mb0 + 8 * b;
-        mbar_expect_tx_arrive(mb, total);
-        for (int r = 0; r < cstage; ++r) {
-            const int c = st * cstage + r;
-            if (c < a.nchan && m[r].bytes > 0) {
-                int64_t first, bytes;
-                window(c, &first, &bytes);
-                const uint8_t *src = a.in + (int64_t)c * a.in_pitch_b + first * ELEM;
-                bulk_g2s(smem_addr(buf + r * row_bytes), src, (uint32_t)m[r].bytes, mb);
-            }
-        }
-    };
-
-    if (tid == 0)
-        issue(0, 0);
-
-    // Accumulators.
-    uint32_t L1[DT][kWords], L2[DT][kWords];  // uint8 SWAR
+    uint32_t L1[DT][kWords], L2[DT][kWords];                            // uint8 SWAR
     float P[DT][kWords][SPW], S[DT][kWords][SPW], C[DT][kWords][SPW];  // floats
 #pragma unroll
     for (int j = 0; j < DT; ++j)
@@ -310,8 +394,8 @@ __global__ void __launch_bounds__(512, 1) dedisperse_kernel(const KArgs a) {
 #pragma unroll
             for (int k = 0; k < kWords; ++k) {
                 const uint32_t lo = L1[j][k] - (L2[j][k] << 8);
-                float4 v = make_float4((float)(lo & 0xffffu), (float)(L2[j][k] & 0xffffu),
-                                       (float)(lo >> 16), (float)(L2[j][k] >> 16));
+                const float4 v = make_float4((float)(lo & 0xffffu), (float)(L2[j][k] & 0xffffu),
+                                             (float)(lo >> 16), (float)(L2[j][k] >> 16));
                 L1[j][k] = 0u;
                 L2[j][k] = 0u;
                 if (row >= 0) {
@@ -345,56 +429,11 @@ __global__ void __launch_bounds__(512, 1) dedisperse_kernel(const KArgs a) {
     };
 
     for (int st = 0; st < nstage; ++st) {
-        const int b = st & 1;
-        const uint32_t mb = mb0 + 8 * b;
-        uint8_t *buf = smem + b * stage_bytes;
-        const RowMeta *m = meta + b * cstage;
-
-        bool failed = !mbar_wait(mb, (st >> 1) & 1);
-        if (!failed) {
-            // Padding rows: zeros where the threads will read (shift 0).
-            for (int r = 0; r < cstage; ++r) {
-                if (m[r].bytes == 0) {
-                    uint4 *z = reinterpret_cast<uint4 *>(buf + r * row_bytes);
-                    const int n16 = (ELEM * t_cta + 16) / 16;
-                    for (int g = tid; g < n16; g += nthreads)
-                        z[g] = make_uint4(0, 0, 0, 0);
-                }
-            }
-            // Re-aligned copies of each row (phases 1..NPH-1).
-            if (NPH > 1) {
-                for (int r = 0; r < cstage; ++r) {
-                    const int n16 = m[r].bytes >> 4;
-                    uint8_t *ph0 = buf + r * row_bytes;
-                    for (int g = tid; g < n16; g += nthreads) {
-                        const uint4 v = *reinterpret_cast<const uint4 *>(ph0 + 16 * g);
-                        const uint32_t nx = *reinterpret_cast<const uint32_t *>(ph0 + 16 * g + 16);
-#pragma unroll
-                        for (int p = 1; p < NPH; ++p) {
-                            const uint32_t sel = (ELEM == 1)
-                                                     ? (0x3210u + 0x1111u * (uint32_t)p)
-                                                     : 0x5432u;
-                            uint4 o;
-                            o.x = prmt(v.x, v.y, sel);
-                            o.y = prmt(v.y, v.z, sel);
-                            o.z = prmt(v.z, v.w, sel);
-                            o.w = prmt(v.w, nx, sel);
-                            *reinterpret_cast<uint4 *>(ph0 + p * wp + 16 * g) = o;
-                        }
-                    }
-                }
-            }
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        }
-        if (__syncthreads_or(failed)) {
+        const int b = st % nst;
+        if (!mbar_wait(full0 + 8 * b, (st / nst) & 1)) {
             record(a.status, kDevTimeout);
-            mbar_wait(mb, (st >> 1) & 1);  // let this CTA's copies land before leaving
             return;
         }
-        if (tid == 0 && st + 1 < nstage)
-            issue(st + 1, b ^ 1);
-
-        // Flush / block boundary before this stage if it would overflow.
         if (since_flush + cstage > FLUSH) {
             if (ELEM == 1)
                 flush_u8();
@@ -404,6 +443,7 @@ __global__ void __launch_bounds__(512, 1) dedisperse_kernel(const KArgs a) {
         }
         since_flush += cstage;
 
+        const RowMeta *m = meta + b * cstage;
         for (int r = 0; r < cstage; r += 2) {
             const RowMeta m0 = m[r];
             const RowMeta m1 = m[r + 1];
@@ -426,9 +466,9 @@ __global__ void __launch_bounds__(512, 1) dedisperse_kernel(const KArgs a) {
 #pragma unroll
                 for (int k = 0; k < kWords; ++k) {
                     if (ELEM == 1) {
-                        L1[j][k] = iadd3(L1[j][k], x[k], y[k]);
-                        L2[j][k] = iadd3(L2[j][k], prmt(x[k], 0u, 0x4341u),
-                                         prmt(y[k], 0u, 0x4341u));
+                        L1[j][k] = L1[j][k] + x[k] + y[k];
+                        L2[j][k] = imad_acc(prmt(x[k], 0u, 0x4341u), one, L2[j][k]);
+                        L2[j][k] = imad_acc(prmt(y[k], 0u, 0x4341u), one, L2[j][k]);
                     } else if (ELEM == 2) {
                         P[j][k][0] = add_f16_lo(y[k], add_f16_lo(x[k], P[j][k][0]));
                         P[j][k][SPW - 1] = add_f16_hi(y[k], add_f16_hi(x[k], P[j][k][SPW - 1]));
@@ -439,6 +479,9 @@ __global__ void __launch_bounds__(512, 1) dedisperse_kernel(const KArgs a) {
                 }
             }
         }
+        __syncwarp();
+        if (lane == 0)
+            mbar_arrive(empty0 + 8 * b);
     }
 
     if (ELEM == 1) {
@@ -481,16 +524,33 @@ cudaError_t launch_t(const KArgs &a, const Geometry &g, int64_t ntiles, cudaStre
     return cudaGetLastError();
 }
 
+template <int ELEM>
+cudaError_t launch_planes(const uint8_t *in, int64_t pitch_b, int nchan, int64_t nsamp_in,
+                          uint8_t *planes, int64_t plane_stride, cudaStream_t s) {
+    const int64_t groups = (nsamp_in * ELEM + 15) / 16;
+    const int64_t total = groups * nchan;
+    const int64_t blocks = std::min<int64_t>((total + 255) / 256, 152 * 16);
+    phase_planes_kernel<ELEM><<<(unsigned)blocks, 256, 0, s>>>(in, pitch_b, nchan, groups, planes,
+                                                               plane_stride);
+    return cudaGetLastError();
+}
+
 }  // namespace
+
+int64_t scratch_bytes(dd_dtype dtype, int nchan, int64_t in_pitch_b) {
+    return (int64_t)(phases(dtype) - 1) * nchan * in_pitch_b;
+}
 
 dd_status launch_dedisperse(dd_plan_s *p, const Geometry &g, const DevTables &dt, const void *in,
                             dd_dtype dtype, int64_t in_pitch, int64_t nsamp_in, float *out,
-                            int64_t out_pitch, int64_t nsamp_out, void *stream) {
+                            int64_t out_pitch, int64_t nsamp_out, void *scratch, void *stream) {
     if (nsamp_out == 0)
         return DD_OK;
     KArgs a;
     a.in = static_cast<const uint8_t *>(in);
     a.in_pitch_b = in_pitch * g.elem;
+    a.planes = static_cast<const uint8_t *>(scratch);
+    a.plane_stride = (int64_t)p->nchan * a.in_pitch_b;
     a.nsamp_in = nsamp_in;
     a.out = out;
     a.out_pitch = out_pitch;
@@ -499,18 +559,35 @@ dd_status launch_dedisperse(dd_plan_s *p, const Geometry &g, const DevTables &dt
     a.dm_sorted = dt.dm_sorted;
     a.perm = dt.perm;
     a.nchan = p->nchan;
-    a.ndm_pad = dt.ndm_pad;
     a.dm_warps = g.tiles.dm_warps;
+    a.time_warps = g.tiles.time_warps;
     a.ntile_d = g.ntile_d;
     a.cstage = g.tiles.chan_per_stage;
+    a.nstages = g.nstages;
     a.wp = g.wp;
+    a.zero_bytes = g.zero_bytes;
+    a.one = 1u;
     a.status = dt.status;
     const int64_t ntile_t = (nsamp_out + g.t_cta - 1) / g.t_cta;
     const int64_t ntiles = ntile_t * g.ntile_d;
     if (ntiles > 0x7fffffffLL)
         return fail(DD_ERR_INVALID, "too many tiles for one launch");
+    if (g.nph > 1 && scratch == nullptr)
+        return fail(DD_ERR_INVALID, "phase-plane scratch missing");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    cudaError_t e = cudaErrorInvalidValue;
+    cudaError_t e = cudaSuccess;
+    int launches = 1;
+    if (dtype == DD_U8) {
+        e = launch_planes<1>(a.in, a.in_pitch_b, p->nchan, nsamp_in, (uint8_t *)scratch,
+                             a.plane_stride, s);
+        ++launches;
+    } else if (dtype == DD_F16) {
+        e = launch_planes<2>(a.in, a.in_pitch_b, p->nchan, nsamp_in, (uint8_t *)scratch,
+                             a.plane_stride, s);
+        ++launches;
+    }
+    if (e != cudaSuccess)
+        return fail(DD_ERR_CUDA, std::string("phase-plane launch failed: ") + cudaGetErrorString(e));
     const int dthr = g.tiles.dm_per_thread;
     switch (dtype) {
     case DD_U8:
@@ -528,7 +605,7 @@ dd_status launch_dedisperse(dd_plan_s *p, const Geometry &g, const DevTables &dt
     }
     if (e != cudaSuccess)
         return fail(DD_ERR_CUDA, std::string("kernel launch failed: ") + cudaGetErrorString(e));
-    count_launch();
+    count_launch(launches);
     return DD_OK;
 }
 

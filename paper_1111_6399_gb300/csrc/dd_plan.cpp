@@ -52,9 +52,9 @@ void count_launch(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
 dd_tiles default_tiles(dd_dtype t) {
     switch (t) {
-    case DD_U8:  return dd_tiles{4, 16, 1, 8};
-    case DD_F16: return dd_tiles{1, 16, 1, 16};
-    default:     return dd_tiles{2, 16, 1, 16};
+    case DD_U8:  return dd_tiles{4, 12, 1, 8};
+    case DD_F16: return dd_tiles{1, 12, 1, 16};
+    default:     return dd_tiles{2, 12, 1, 16};
     }
 }
 
@@ -65,7 +65,7 @@ std::vector<dd_tiles> auto_tiles(dd_dtype t) {
     for (int dcta = base.dm_per_thread * base.dm_warps; dcta >= 1; dcta /= 2) {
         const int dthr = std::min(base.dm_per_thread, dcta);
         const int wd = dcta / dthr;
-        const int wt = std::max(1, std::min(16 / wd, max_t_cta / warp_span(t)));
+        const int wt = std::max(1, std::min(kMaxConsumerWarps / wd, max_t_cta / warp_span(t)));
         for (int cs = base.chan_per_stage; cs >= 2; cs /= 2)
             out.push_back(dd_tiles{dthr, wd, wt, cs});
     }
@@ -77,9 +77,10 @@ dd_status make_geometry(dd_plan_s *p, dd_dtype t, const dd_tiles &tl, Geometry *
         return fail(DD_ERR_INVALID, "unknown dtype");
     const int dthr = tl.dm_per_thread;
     bool ok_dthr = dthr == 1 || dthr == 2 || dthr == 4;
-    if (!ok_dthr || tl.dm_warps < 1 || tl.time_warps < 1 || tl.dm_warps * tl.time_warps > 16)
+    if (!ok_dthr || tl.dm_warps < 1 || tl.time_warps < 1 ||
+        tl.dm_warps * tl.time_warps > kMaxConsumerWarps)
         return fail(DD_ERR_INVALID, "tile shape: dm_per_thread must be 1, 2 or 4 and "
-                                    "dm_warps*time_warps in 1..16");
+                                    "dm_warps*time_warps in 1..12");
     if (tl.chan_per_stage < 2 || tl.chan_per_stage > 64 || (tl.chan_per_stage & 1))
         return fail(DD_ERR_INVALID, "tile shape: chan_per_stage must be even, 2..64");
     const int limit = (t == DD_U8) ? kSwarChannels : kFloatBlock;
@@ -111,15 +112,25 @@ dd_status make_geometry(dd_plan_s *p, dd_dtype t, const dd_tiles &tl, Geometry *
             widest = std::max(widest, w);
         }
     }
-    int64_t wp = widest + 16;  // one spare 16-byte group for the phase build
-    int64_t stage = (int64_t)tl.chan_per_stage * r.nph * wp;
-    int64_t smem = 2 * stage + 2 * tl.chan_per_stage * 16 + 16;
+    const int64_t wp = widest + 16;
+    const int64_t zero_bytes = ((int64_t)r.elem * r.t_cta + 16 + 15) / 16 * 16;
+    auto smem_for = [&](int64_t n) {
+        return n * tl.chan_per_stage * r.nph * wp + n * tl.chan_per_stage * 16 + zero_bytes +
+               16 * n;
+    };
+    int nst = 4;
+    while (nst > 2 && smem_for(nst) > kMaxSmem)
+        --nst;
+    const int64_t smem = smem_for(nst);
     if (smem > kMaxSmem)
         return fail(DD_ERR_INVALID, "tile shape: staged window needs " + std::to_string(smem) +
                                         " bytes of shared memory (limit 232448); use fewer "
                                         "channels per stage or fewer DMs per CTA");
     r.wp = (int)wp;
+    r.nstages = nst;
+    r.zero_bytes = (int)zero_bytes;
     r.smem = (int)smem;
+    r.threads += 32;  // producer warp
     *g = r;
     return DD_OK;
 }
@@ -270,6 +281,11 @@ void dd_plan_destroy(dd_plan_t p) {
     cudaGetDevice(&cur);
     for (auto &kv : p->dev) {
         cudaSetDevice(kv.first);
+        if (kv.second.scratch_done)
+            cudaEventSynchronize((cudaEvent_t)kv.second.scratch_done);
+        cudaFree(kv.second.scratch);
+        if (kv.second.scratch_done)
+            cudaEventDestroy((cudaEvent_t)kv.second.scratch_done);
         cudaFree(kv.second.dmshift);
         cudaFree(kv.second.dm_sorted);
         cudaFree(kv.second.perm);

@@ -82,8 +82,8 @@ def test_small_workload_bit_exact(dd, oracle_lib):
     assert np.array_equal(got, want)
 
 
-TILES_U8 = [(4, 16, 1, 8), (4, 4, 2, 8), (2, 3, 1, 2), (1, 1, 1, 16), (4, 5, 3, 4),
-            (2, 8, 1, 32), (1, 16, 1, 64)]
+TILES_U8 = [(4, 12, 1, 8), (4, 4, 2, 8), (2, 3, 1, 2), (1, 1, 1, 16), (4, 5, 2, 4),
+            (2, 8, 1, 32), (1, 12, 1, 64), (4, 6, 1, 2)]
 
 
 @pytest.mark.parametrize("tiles", TILES_U8)
