@@ -141,6 +141,13 @@ dd_status dd_execute_host(dd_plan_t plan, const void *in_host, dd_dtype dtype,
  * DD_ERR_TIMEOUT or DD_ERR_DEVICE), then clear it. */
 dd_status dd_sync(dd_plan_t plan, void *stream);
 
+/* Profiling hook: while set (non-NULL), every execution issued from this
+ * thread records start_event just before its de-dispersion kernel and
+ * stop_event just after it, on the launch stream (cudaEvent_t handles owned
+ * by the caller; the phase-plane pre-pass falls outside the pair).  Pass
+ * NULLs to clear. */
+void dd_profile_events(void *start_event, void *stop_event);
+
 /* Kernel launches made by this process so far (all entry points). */
 int64_t dd_launch_count(void);
 

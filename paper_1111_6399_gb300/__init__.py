@@ -3,10 +3,10 @@
 The compute path is libdd.so (hand-written sm_103a CUDA behind a C ABI, see
 include/dd.h); this package is its thin Python binding.  Importing it loads
 the library and raises ImportError if it has not been built
-(``python -m paper_1111_6399_gb300.build``).
+(``python __graft_entry__.py``).
 """
 from ._binding import (DD_F16, DD_F32, DD_U8, DDError, Plan, Tiles, check, dtype_code,
-                       elem_size, launch_count, lib, warp_span)
+                       elem_size, launch_count, lib, profile_events, warp_span)
 
 __all__ = ["Plan", "Tiles", "DDError", "DD_U8", "DD_F16", "DD_F32", "check", "dtype_code",
-           "elem_size", "warp_span", "launch_count", "lib"]
+           "elem_size", "warp_span", "launch_count", "profile_events", "lib"]

@@ -25,7 +25,7 @@ DD_ERR_NOMEM, DD_ERR_BUSY, DD_ERR_TIMEOUT, DD_ERR_DEVICE = -3, -4, -5, -6
 EXPORTS = [
     "dd_plan", "dd_plan_destroy", "dd_plan_maxshift", "dd_plan_nchan", "dd_plan_ndm",
     "dd_plan_dmshift", "dd_plan_get_tiles", "dd_plan_set_tiles", "dd_execute",
-    "dd_execute_host", "dd_sync", "dd_launch_count", "dd_last_error",
+    "dd_execute_host", "dd_sync", "dd_profile_events", "dd_launch_count", "dd_last_error",
 ]
 
 
@@ -46,7 +46,7 @@ class Tiles(ctypes.Structure):
 def _load() -> ctypes.CDLL:
     if not os.path.exists(LIB_PATH):
         raise ImportError(f"libdd.so not built ({LIB_PATH}); run "
-                          "python -m paper_1111_6399_gb300.build")
+                          "python __graft_entry__.py")
     lib = ctypes.CDLL(LIB_PATH)
     p, i64, i32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int
     sig = {
@@ -62,6 +62,7 @@ def _load() -> ctypes.CDLL:
         "dd_execute": (i32, [p, p, i32, i64, i64, p, i64, i64, p]),
         "dd_execute_host": (i32, [p, p, i32, i64, i64, p, i64, i64]),
         "dd_sync": (i32, [p, p]),
+        "dd_profile_events": (None, [p, p]),
         "dd_launch_count": (i64, []),
         "dd_last_error": (ctypes.c_char_p, []),
     }
@@ -101,6 +102,12 @@ def warp_span(code: int) -> int:
 
 def launch_count() -> int:
     return int(lib.dd_launch_count())
+
+
+def profile_events(start=None, stop=None) -> None:
+    """dd_profile_events with torch.cuda.Event objects (None clears)."""
+    h = (lambda e: ctypes.c_void_p(e.cuda_event) if e is not None else None)
+    lib.dd_profile_events(h(start), h(stop))
 
 
 class Plan:

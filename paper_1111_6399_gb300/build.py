@@ -1,7 +1,7 @@
 """Build libdd.so in-tree for sm_103a (no cmake; a few translation units in
 parallel).
 
-    python -m paper_1111_6399_gb300.build        # or build() from Python
+    python __graft_entry__.py      (loads this file by path; see build())
 
 Outputs paper_1111_6399_gb300/_build/libdd.so.  Host sources are compiled by
 g++ with -ffp-contract=off (the FP64 delay table must not be contracted into

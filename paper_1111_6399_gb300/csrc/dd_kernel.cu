@@ -535,6 +535,9 @@ cudaError_t launch_planes(const uint8_t *in, int64_t pitch_b, int nchan, int64_t
     return cudaGetLastError();
 }
 
+thread_local cudaEvent_t g_prof_start = nullptr;
+thread_local cudaEvent_t g_prof_stop = nullptr;
+
 }  // namespace
 
 int64_t scratch_bytes(dd_dtype dtype, int nchan, int64_t in_pitch_b) {
@@ -589,6 +592,8 @@ dd_status launch_dedisperse(dd_plan_s *p, const Geometry &g, const DevTables &dt
     if (e != cudaSuccess)
         return fail(DD_ERR_CUDA, std::string("phase-plane launch failed: ") + cudaGetErrorString(e));
     const int dthr = g.tiles.dm_per_thread;
+    if (g_prof_start)
+        cudaEventRecord(g_prof_start, s);
     switch (dtype) {
     case DD_U8:
         e = dthr == 1 ? launch_t<1, 1>(a, g, ntiles, s)
@@ -605,8 +610,15 @@ dd_status launch_dedisperse(dd_plan_s *p, const Geometry &g, const DevTables &dt
     }
     if (e != cudaSuccess)
         return fail(DD_ERR_CUDA, std::string("kernel launch failed: ") + cudaGetErrorString(e));
+    if (g_prof_stop)
+        cudaEventRecord(g_prof_stop, s);
     count_launch(launches);
     return DD_OK;
 }
 
 }  // namespace dd
+
+extern "C" void dd_profile_events(void *start_event, void *stop_event) {
+    dd::g_prof_start = static_cast<cudaEvent_t>(start_event);
+    dd::g_prof_stop = static_cast<cudaEvent_t>(stop_event);
+}

@@ -258,4 +258,4 @@ def test_launch_count_and_status(dd):
     out = torch.empty((2, 512), device="cuda")
     plan.execute(x, out)
     plan.sync()
-    assert dd.launch_count() == n0 + 1
+    assert dd.launch_count() == n0 + 2  # phase planes + de-dispersion
