@@ -222,6 +222,9 @@ def run_ours(args, w):
           for _ in range(args.steps)]
     kev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
            for _ in range(args.steps)]
+    for a, b in kev:  # torch only times events it has seen recorded; the library re-records
+        a.record(stream)
+        b.record(stream)
     n0 = dd.launch_count()
     with ClockSampler(local) as clk:
         barrier()
