@@ -205,6 +205,16 @@ def run_ours(args, w):
     out = torch.empty((w.ndm, w.nsamp_out), dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream(dev)
 
+    tune = None
+    if args.tiles:
+        plan.set_tiles("u8", *[int(v) for v in args.tiles.split(",")])
+    elif not args.no_tune:
+        tune = plan.autotune(x, out, nsamp_in=nin, stream=stream, reps=2)
+        if rank == 0:
+            for tl, ms in sorted(tune, key=lambda r: (r[1] < 0, r[1])):
+                print(f"# tune {tl} {ms:.3f} ms" if ms >= 0 else f"# tune {tl} rejected",
+                      file=sys.stderr)
+
     def step():
         plan.execute(x, out, nsamp_in=nin, stream=stream)
 
@@ -278,6 +288,8 @@ def run_ours(args, w):
         "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
         "config": {"workload": w.name, "nchan": w.nchan, "ndm": w.ndm,
                    "nsamp_out": w.nsamp_out, "maxshift": S, "tiles": plan.get_tiles("u8"),
+                   "tiles_from": "fixed" if args.tiles else ("default" if args.no_tune
+                                                             else "autotuner"),
                    "l2": "inputs larger than L2 (151 MB in + 537 MB out per step)",
                    "parallelism": f"replicas{world}" if world > 1 else "single-gpu"},
         "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_adds / 1e12,
@@ -310,6 +322,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="lband", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--no-tune", action="store_true", help="use the plan's default tile shape")
+    ap.add_argument("--tiles", default="", help="fixed tile shape dthr,dm_warps,time_warps,cstage")
     args = ap.parse_args()
     w = WORKLOADS[args.workload]
     if args.impl == "reference":

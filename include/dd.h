@@ -72,8 +72,9 @@ typedef struct dd_plan_s *dd_plan_t;
 /* Tile shape of the de-dispersion kernel (chosen by the plan or the autotuner).
  *   dm_per_thread    trial DMs each thread accumulates (register accumulators)
  *   dm_warps         warps of a CTA along the DM axis
- *   time_warps       warps of a CTA along the time axis (dm_warps*time_warps <= 12;
- *                    the CTA has one more warp that stages the data)
+ *   time_warps       warps of a CTA along the time axis (dm_warps*time_warps <= 16,
+ *                    <= 12 with 4 DMs per thread; the CTA has one more warp
+ *                    that stages the data)
  *   chan_per_stage   channels staged in shared memory per pipeline stage
  * A CTA covers dm_per_thread*dm_warps DMs and time_warps*span samples, where
  * span = 1024 (uint8), 512 (FP16) or 256 (FP32) samples per warp. */
@@ -113,6 +114,26 @@ dd_status dd_plan_get_tiles(dd_plan_t plan, dd_dtype dtype, dd_tiles *tiles_out)
 /* Override the tile shape for dtype (validated: shared-memory fit, supported
  * dm_per_thread).  Not thread-safe against concurrent executions of the plan. */
 dd_status dd_plan_set_tiles(dd_plan_t plan, dd_dtype dtype, const dd_tiles *tiles);
+
+/* One autotuner measurement. */
+typedef struct dd_tune_result {
+    dd_tiles tiles;
+    float ms;          /* best of the timed runs; < 0 if the shape was rejected */
+} dd_tune_result;
+
+/* Autotuner: time every candidate tile shape for dtype on the caller's
+ * buffers (same arguments and rules as dd_execute; out is overwritten), keep
+ * the fastest as the plan's shape for dtype, and optionally report each
+ * candidate (results may be NULL; at most max_results are written, *n_results
+ * receives the number measured).  Each candidate runs `reps` timed
+ * executions after one warm-up on stream; the call synchronizes stream.
+ * Candidates: DMs per thread 1/2/4 x DM warps x time warps x channels per
+ * stage, filtered by the shared-memory fit.  Not thread-safe against
+ * concurrent executions of the plan. */
+dd_status dd_autotune(dd_plan_t plan, const void *in, dd_dtype dtype, int64_t in_pitch,
+                      int64_t nsamp_in, float *out, int64_t out_pitch, int64_t nsamp_out,
+                      void *stream, int reps, dd_tune_result *results, int max_results,
+                      int *n_results);
 
 /* --- single-beam execution (Sec. 3: the GPU kernel) ---------------------- */
 

@@ -26,6 +26,7 @@ EXPORTS = [
     "dd_plan", "dd_plan_destroy", "dd_plan_maxshift", "dd_plan_nchan", "dd_plan_ndm",
     "dd_plan_dmshift", "dd_plan_get_tiles", "dd_plan_set_tiles", "dd_execute",
     "dd_execute_host", "dd_sync", "dd_profile_events", "dd_launch_count", "dd_last_error",
+    "dd_autotune",
 ]
 
 
@@ -41,6 +42,10 @@ class Tiles(ctypes.Structure):
 
     def as_tuple(self):
         return (self.dm_per_thread, self.dm_warps, self.time_warps, self.chan_per_stage)
+
+
+class TuneResult(ctypes.Structure):
+    _fields_ = [("tiles", Tiles), ("ms", ctypes.c_float)]
 
 
 def _load() -> ctypes.CDLL:
@@ -63,6 +68,8 @@ def _load() -> ctypes.CDLL:
         "dd_execute_host": (i32, [p, p, i32, i64, i64, p, i64, i64]),
         "dd_sync": (i32, [p, p]),
         "dd_profile_events": (None, [p, p]),
+        "dd_autotune": (i32, [p, p, i32, i64, i64, p, i64, i64, p, i32,
+                              ctypes.POINTER(TuneResult), i32, ctypes.POINTER(i32)]),
         "dd_launch_count": (i64, []),
         "dd_last_error": (ctypes.c_char_p, []),
     }
@@ -202,6 +209,22 @@ class Plan:
         check(lib.dd_execute_host(self.handle, inp_np.ctypes.data, code,
                                   inp_np.strides[0] // inp_np.itemsize, nsamp_in,
                                   out_np.ctypes.data, out_np.strides[0] // 4, nsamp_out))
+
+    def autotune(self, inp, out, nsamp_in: int | None = None, nsamp_out: int | None = None,
+                 stream=None, reps: int = 2) -> list:
+        """dd_autotune on torch CUDA tensors; returns [(tiles, ms), ...] for every
+        candidate (ms < 0: rejected) and leaves the fastest shape set on the plan."""
+        import torch
+        nsamp_in = inp.shape[1] if nsamp_in is None else nsamp_in
+        nsamp_out = out.shape[1] if nsamp_out is None else nsamp_out
+        s = torch.cuda.current_stream(inp.device) if stream is None else stream
+        res = (TuneResult * 512)()
+        n = ctypes.c_int(0)
+        check(lib.dd_autotune(self.handle, ctypes.c_void_p(inp.data_ptr()), dtype_code(inp.dtype),
+                              inp.stride(0), nsamp_in, ctypes.c_void_p(out.data_ptr()),
+                              out.stride(0), nsamp_out, ctypes.c_void_p(s.cuda_stream), reps,
+                              res, 512, ctypes.byref(n)))
+        return [(res[i].tiles.as_tuple(), float(res[i].ms)) for i in range(min(n.value, 512))]
 
     def sync(self, stream=None) -> None:
         """dd_sync: synchronize the stream and raise if a kernel recorded a failure."""

@@ -7,6 +7,7 @@
 #include <cstring>
 #include <mutex>
 #include <string>
+#include <vector>
 
 #include "dd_internal.h"
 
@@ -245,4 +246,92 @@ extern "C" dd_status dd_execute_host(dd_plan_t p, const void *in_host, dd_dtype 
             return fail(DD_ERR_CUDA, std::string("synchronize: ") + cudaGetErrorString(e));
     }
     return dd_sync(p, nullptr);
+}
+
+// Candidate tile shapes of the autotuner (validated later by make_geometry).
+static std::vector<dd_tiles> tune_candidates(dd_dtype t) {
+    std::vector<dd_tiles> out;
+    const int dthrs[3] = {1, 2, 4};
+    const int dws[6] = {4, 6, 8, 12, 16, 2};
+    const int wts[3] = {1, 2, 4};
+    const int css[4] = {4, 8, 16, 32};
+    for (int dthr : dthrs)
+        for (int dw : dws)
+            for (int wt : wts) {
+                if (dw * wt > dd::max_consumer_warps(dthr) || dw * wt < 4)
+                    continue;
+                for (int cs : css) {
+                    const int limit = t == DD_U8 ? dd::kSwarChannels : dd::kFloatBlock;
+                    if (limit % cs != 0)
+                        continue;
+                    out.push_back(dd_tiles{dthr, dw, wt, cs});
+                }
+            }
+    return out;
+}
+
+extern "C" dd_status dd_autotune(dd_plan_t p, const void *in, dd_dtype dtype, int64_t in_pitch,
+                                 int64_t nsamp_in, float *out, int64_t out_pitch,
+                                 int64_t nsamp_out, void *stream, int reps,
+                                 dd_tune_result *results, int max_results, int *n_results) {
+    if (!p)
+        return fail(DD_ERR_INVALID, "plan is NULL");
+    dd_status st = check_layout(p, dtype, in_pitch, nsamp_in, out_pitch, nsamp_out, true);
+    if (st != DD_OK)
+        return st;
+    if (nsamp_out == 0 || reps < 1)
+        return fail(DD_ERR_INVALID, "autotune needs nsamp_out > 0 and reps >= 1");
+    if (!in || !out || !aligned16(in) || !aligned16(out))
+        return fail(DD_ERR_INVALID, "in and out must be non-NULL and 16-byte aligned");
+    dd::DevTables *dt = nullptr;
+    if ((st = dd::device_tables(p, &dt)) != DD_OK)
+        return st;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+        return fail(DD_ERR_CUDA, "event creation failed");
+    float best = -1.0f;
+    dd_tiles best_tiles{};
+    int n = 0;
+    for (const dd_tiles &cand : tune_candidates(dtype)) {
+        dd::Geometry g;
+        float ms = -1.0f;
+        if (dd::make_geometry(p, dtype, cand, &g) == DD_OK) {
+            st = dd::run_with_plan_scratch(p, g, *dt, in, dtype, in_pitch, nsamp_in, out,
+                                           out_pitch, nsamp_out, s);  // warm-up
+            for (int r = 0; r < reps && st == DD_OK; ++r) {
+                cudaEventRecord(e0, s);
+                st = dd::run_with_plan_scratch(p, g, *dt, in, dtype, in_pitch, nsamp_in, out,
+                                               out_pitch, nsamp_out, s);
+                cudaEventRecord(e1, s);
+                if (cudaEventSynchronize(e1) != cudaSuccess) {
+                    st = fail(DD_ERR_CUDA, "autotune synchronize failed");
+                    break;
+                }
+                float t = 0.0f;
+                cudaEventElapsedTime(&t, e0, e1);
+                ms = (ms < 0.0f || t < ms) ? t : ms;
+            }
+            if (st != DD_OK)
+                break;
+            if (ms >= 0.0f && (best < 0.0f || ms < best)) {
+                best = ms;
+                best_tiles = cand;
+            }
+        }
+        if (results && n < max_results)
+            results[n] = dd_tune_result{cand, ms};
+        ++n;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (n_results)
+        *n_results = n;
+    if (st != DD_OK)
+        return st;
+    if (best < 0.0f)
+        return fail(DD_ERR_INVALID, "no candidate tile shape fits this plan");
+    if ((st = dd_sync(p, stream)) != DD_OK)
+        return st;
+    return dd_plan_set_tiles(p, dtype, &best_tiles);
 }

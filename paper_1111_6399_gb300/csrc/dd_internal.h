@@ -26,9 +26,18 @@ constexpr int kSwarChannels = 256;
 constexpr int kFloatBlock = 64;
 
 constexpr int kMaxSmem = 232448;  // 227 KB dynamic shared memory per CTA
-// Consumer warps per CTA (plus one producer warp).  13 warps put at most 4
-// on each SM sub-partition, which leaves 128 registers per thread.
-constexpr int kMaxConsumerWarps = 12;
+// Consumer warps per CTA (plus one producer warp).  With 4 DMs per thread
+// the accumulators need ~128 registers, so 12 + 1 warps (at most 4 per SM
+// sub-partition); with 1-2 DMs per thread 16 + 1 warps fit in 96 registers.
+constexpr int kMaxConsumerWarps = 16;
+#ifdef __CUDACC__
+#define DD_HD __host__ __device__
+#else
+#define DD_HD
+#endif
+DD_HD constexpr int max_consumer_warps(int dm_per_thread) {
+    return dm_per_thread >= 4 ? 12 : 16;
+}
 
 // Device status word values (written by kernels, read by dd_sync).
 constexpr int kDevOk = 0;

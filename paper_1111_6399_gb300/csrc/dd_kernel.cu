@@ -69,11 +69,6 @@ struct KArgs {
     int *status;
 };
 
-struct __align__(16) RowMeta {
-    int base;     // smem byte offset of window sample t0 (may precede the row)
-    float ds;     // dmshift of the channel (0 for padding rows)
-    int pad0, pad1;
-};
 
 __device__ __forceinline__ uint32_t smem_addr(const void *p) {
     return (uint32_t)__cvta_generic_to_shared(p);
@@ -226,9 +221,17 @@ __global__ void __launch_bounds__(256) phase_planes_kernel(const uint8_t *__rest
 // ---------------------------------------------------------------------------
 // The de-dispersion kernel.  ELEM = bytes per sample (1, 2, 4); DT = DMs per
 // consumer thread.  Warps 0..ncw-1 consume, warp ncw produces.
+//
+// Per stage the producer also writes, for every staged channel row r and
+// every DM k of the CTA, the shared-memory byte offset of that DM's shifted
+// window (row base + ELEM*s(c,k) + phase row), so a consumer fetches its DMs'
+// offsets with one vector LDS instead of recomputing the shift.  Consumers
+// software-pipeline: the 16 words of the next (channel pair, DM) are loaded
+// into the alternate register buffer before the current ones are summed.
 // ---------------------------------------------------------------------------
 template <int ELEM, int DT>
-__global__ void __launch_bounds__(32 * (kMaxConsumerWarps + 1), 1) dedisperse_kernel(const KArgs a) {
+__global__ void __launch_bounds__(32 * (max_consumer_warps(DT) + 1), 1)
+    dedisperse_kernel(const KArgs a) {
     constexpr int NPH = 4 / ELEM;            // phase copies per row
     constexpr int SPW = 4 / ELEM;            // samples per 4-byte word
     constexpr int SPAN = 32 * kWords * SPW;  // samples per warp
@@ -249,8 +252,9 @@ __global__ void __launch_bounds__(32 * (kMaxConsumerWarps + 1), 1) dedisperse_ke
     const int wp = a.wp;
     const int row_bytes = NPH * wp;
     const int stage_bytes = cstage * row_bytes;
-    RowMeta *meta = reinterpret_cast<RowMeta *>(smem + nst * stage_bytes);
-    uint8_t *zero = smem + nst * stage_bytes + nst * cstage * 16;
+    const int tab_stride = cstage * dm_cta;  // ints per stage in the offset table
+    int *atab = reinterpret_cast<int *>(smem + nst * stage_bytes);
+    uint8_t *zero = smem + nst * stage_bytes + ((nst * tab_stride * 4 + 15) & ~15);
     uint64_t *mbar = reinterpret_cast<uint64_t *>(zero + a.zero_bytes);
     const uint32_t full0 = smem_addr(&mbar[0]);
     const uint32_t empty0 = smem_addr(&mbar[nst]);
@@ -274,6 +278,9 @@ __global__ void __launch_bounds__(32 * (kMaxConsumerWarps + 1), 1) dedisperse_ke
         // ------------------------------ producer ------------------------------
         const float dm_min = a.dm_sorted[kcta];
         const float dm_max = a.dm_sorted[kcta + dm_cta - 1];
+        float dmk[2];
+        dmk[0] = a.dm_sorted[kcta + min(lane, dm_cta - 1)];
+        dmk[1] = a.dm_sorted[kcta + min(lane + 32, dm_cta - 1)];
         int issued = 0;
         bool ok = true;
         for (int st = 0; st < nstage; ++st) {
@@ -283,42 +290,51 @@ __global__ void __launch_bounds__(32 * (kMaxConsumerWarps + 1), 1) dedisperse_ke
                 ok = false;
                 break;
             }
-            RowMeta *m = meta + b * cstage;
             uint8_t *buf = smem + b * stage_bytes;
+            int *tab = atab + b * tab_stride;
             uint32_t my_bytes[2] = {0u, 0u};
             int64_t my_first[2] = {0, 0};
+            int my_base[2] = {zero_off, zero_off};
+            float my_ds[2] = {0.0f, 0.0f};
             bool bad = false;
+            // Window of each staged row (lane r holds rows r and r + 32).
             for (int h = 0; h < 2; ++h) {
                 const int r = lane + 32 * h;
-                if (r >= cstage)
-                    break;
                 const int c = st * cstage + r;
-                RowMeta rm;
-                rm.pad0 = rm.pad1 = 0;
-                rm.base = zero_off;
-                rm.ds = 0.0f;
-                if (c < a.nchan) {
-                    const float ds = a.dmshift[c];
-                    const int64_t smin = shift_of(dm_min, ds);
-                    const int64_t smax = shift_of(dm_max, ds);
-                    const int64_t first = (t0 + smin) & ~(int64_t)(16 / ELEM - 1);
-                    int64_t end = t0 + t_cta + smax;
-                    if (end > a.nsamp_in)
-                        end = a.nsamp_in;
-                    const int64_t bytes = ((end - first) * ELEM + 15) & ~(int64_t)15;
-                    if (bytes > wp - 16 || bytes <= 0) {  // excluded by the host checks
-                        bad = true;
-                    } else {
-                        rm.base = (int)(buf + r * row_bytes - smem) + (int)(ELEM * (t0 - first));
-                        rm.ds = ds;
-                        my_bytes[h] = (uint32_t)bytes;
-                        my_first[h] = first;
-                    }
+                if (r >= cstage || c >= a.nchan)
+                    continue;
+                const float ds = a.dmshift[c];
+                const int64_t smin = shift_of(dm_min, ds);
+                const int64_t smax = shift_of(dm_max, ds);
+                const int64_t first = (t0 + smin) & ~(int64_t)(16 / ELEM - 1);
+                int64_t end = t0 + t_cta + smax;
+                if (end > a.nsamp_in)
+                    end = a.nsamp_in;
+                const int64_t bytes = ((end - first) * ELEM + 15) & ~(int64_t)15;
+                if (bytes > wp - 16 || bytes <= 0) {  // excluded by the host checks
+                    bad = true;
+                    continue;
                 }
-                m[r] = rm;
+                my_base[h] = (int)(buf + r * row_bytes - smem) + (int)(ELEM * (t0 - first));
+                my_ds[h] = ds;
+                my_bytes[h] = (uint32_t)bytes;
+                my_first[h] = first;
             }
             if (bad)
                 record(a.status, kDevCheck);
+            // Offset table: row r, DM k -> smem offset of the shifted window.
+            for (int r = 0; r < cstage; ++r) {
+                const int base = __shfl_sync(0xffffffffu, my_base[r >> 5], r & 31);
+                const float ds = __shfl_sync(0xffffffffu, my_ds[r >> 5], r & 31);
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int k = lane + 32 * h;
+                    if (k < dm_cta) {
+                        const int s = shift_of(dmk[h], ds);
+                        tab[r * dm_cta + k] = base + ELEM * s + (s & (NPH - 1)) * (wp - ELEM);
+                    }
+                }
+            }
             uint32_t total = (my_bytes[0] + my_bytes[1]) * NPH;
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1)
@@ -360,10 +376,7 @@ __global__ void __launch_bounds__(32 * (kMaxConsumerWarps + 1), 1) dedisperse_ke
     const int wdi = warp % a.dm_warps;
     const int wti = warp / a.dm_warps;
     const int kthr = kcta + wdi * DT;
-    float dm[DT];
-#pragma unroll
-    for (int j = 0; j < DT; ++j)
-        dm[j] = a.dm_sorted[kthr + j];
+    const int kw = wdi * DT;  // this thread's first DM column in the offset table
     const int thr_off = ELEM * (wti * SPAN) + 4 * lane;
     const uint32_t one = a.one;
 
@@ -428,12 +441,69 @@ __global__ void __launch_bounds__(32 * (kMaxConsumerWarps + 1), 1) dedisperse_ke
                 }
     };
 
-    for (int st = 0; st < nstage; ++st) {
-        const int b = st % nst;
-        if (!mbar_wait(full0 + 8 * b, (st / nst) & 1)) {
+    // Offsets of this thread's DT DMs in rows 2q and 2q+1 of stage buffer b.
+    auto pair_offsets = [&](int b, int q, int (&o0)[DT], int (&o1)[DT]) {
+        const int *r0 = atab + b * tab_stride + (2 * q) * dm_cta + kw;
+        const int *r1 = r0 + dm_cta;
+        if (DT == 4) {
+            const int4 u = *reinterpret_cast<const int4 *>(r0);
+            const int4 v = *reinterpret_cast<const int4 *>(r1);
+            o0[0] = u.x; o0[DT > 1 ? 1 : 0] = u.y; o0[DT > 2 ? 2 : 0] = u.z; o0[DT > 3 ? 3 : 0] = u.w;
+            o1[0] = v.x; o1[DT > 1 ? 1 : 0] = v.y; o1[DT > 2 ? 2 : 0] = v.z; o1[DT > 3 ? 3 : 0] = v.w;
+        } else if (DT == 2) {
+            const int2 u = *reinterpret_cast<const int2 *>(r0);
+            const int2 v = *reinterpret_cast<const int2 *>(r1);
+            o0[0] = u.x; o0[DT > 1 ? 1 : 0] = u.y;
+            o1[0] = v.x; o1[DT > 1 ? 1 : 0] = v.y;
+        } else {
+            o0[0] = r0[0];
+            o1[0] = r1[0];
+        }
+#pragma unroll
+        for (int j = 0; j < DT; ++j) {
+            o0[j] += thr_off;
+            o1[j] += thr_off;
+        }
+    };
+    auto load_words = [&](int off0, int off1, uint32_t (&x)[kWords], uint32_t (&y)[kWords]) {
+        const uint32_t *p0 = reinterpret_cast<const uint32_t *>(smem + off0);
+        const uint32_t *p1 = reinterpret_cast<const uint32_t *>(smem + off1);
+#pragma unroll
+        for (int k = 0; k < kWords; ++k) {
+            x[k] = p0[32 * k];
+            y[k] = p1[32 * k];
+        }
+    };
+    auto accumulate = [&](int j, const uint32_t (&x)[kWords], const uint32_t (&y)[kWords]) {
+#pragma unroll
+        for (int k = 0; k < kWords; ++k) {
+            if (ELEM == 1) {
+                L1[j][k] = L1[j][k] + x[k] + y[k];
+                L2[j][k] = imad_acc(prmt(x[k], 0u, 0x4341u), one, L2[j][k]);
+                L2[j][k] = imad_acc(prmt(y[k], 0u, 0x4341u), one, L2[j][k]);
+            } else if (ELEM == 2) {
+                P[j][k][0] = add_f16_lo(y[k], add_f16_lo(x[k], P[j][k][0]));
+                P[j][k][SPW - 1] = add_f16_hi(y[k], add_f16_hi(x[k], P[j][k][SPW - 1]));
+            } else {
+                P[j][k][0] = __fadd_rn(__fadd_rn(P[j][k][0], __uint_as_float(x[k])),
+                                       __uint_as_float(y[k]));
+            }
+        }
+    };
+
+    const int npairs = cstage / 2;
+    int A0[DT], A1[DT], B0[DT], B1[DT];
+    uint32_t xa[kWords], ya[kWords], xb[kWords], yb[kWords];
+    if (nstage > 0) {
+        if (!mbar_wait(full0, 0)) {
             record(a.status, kDevTimeout);
             return;
         }
+        pair_offsets(0, 0, A0, A1);
+        load_words(A0[0], A1[0], xa, ya);
+    }
+    for (int st = 0; st < nstage; ++st) {
+        const int b = st % nst;
         if (since_flush + cstage > FLUSH) {
             if (ELEM == 1)
                 flush_u8();
@@ -442,41 +512,44 @@ __global__ void __launch_bounds__(32 * (kMaxConsumerWarps + 1), 1) dedisperse_ke
             since_flush = 0;
         }
         since_flush += cstage;
-
-        const RowMeta *m = meta + b * cstage;
-        for (int r = 0; r < cstage; r += 2) {
-            const RowMeta m0 = m[r];
-            const RowMeta m1 = m[r + 1];
-            const int B0 = m0.base + thr_off;
-            const int B1 = m1.base + thr_off;
+        for (int q = 0; q < npairs; ++q) {
+            bool have_next = true;
+            if (q + 1 < npairs) {
+                pair_offsets(b, q + 1, B0, B1);
+            } else if (st + 1 < nstage) {
+                const int bn = (st + 1) % nst;
+                if (!mbar_wait(full0 + 8 * bn, ((st + 1) / nst) & 1)) {
+                    record(a.status, kDevTimeout);
+                    return;
+                }
+                pair_offsets(bn, 0, B0, B1);
+            } else {
+                have_next = false;
+            }
 #pragma unroll
             for (int j = 0; j < DT; ++j) {
-                const int s0 = shift_of(dm[j], m0.ds);
-                const int s1 = shift_of(dm[j], m1.ds);
-                const int a0 = B0 + ELEM * s0 + (s0 & (NPH - 1)) * (wp - ELEM);
-                const int a1 = B1 + ELEM * s1 + (s1 & (NPH - 1)) * (wp - ELEM);
-                const uint32_t *p0 = reinterpret_cast<const uint32_t *>(smem + a0);
-                const uint32_t *p1 = reinterpret_cast<const uint32_t *>(smem + a1);
-                uint32_t x[kWords], y[kWords];
+                // Alternate register buffers: even j reads (xa,ya), odd j (xb,yb).
+                uint32_t (&cx)[kWords] = (j & 1) ? xb : xa;
+                uint32_t (&cy)[kWords] = (j & 1) ? yb : ya;
+                uint32_t (&nx)[kWords] = (j & 1) ? xa : xb;
+                uint32_t (&ny)[kWords] = (j & 1) ? ya : yb;
+                if (j + 1 < DT)
+                    load_words(A0[j + 1 < DT ? j + 1 : 0], A1[j + 1 < DT ? j + 1 : 0], nx, ny);
+                else if (have_next)
+                    load_words(B0[0], B1[0], nx, ny);
+                accumulate(j, cx, cy);
+            }
+            if (DT & 1) {  // odd DT: the next words landed in (xb,yb)
 #pragma unroll
                 for (int k = 0; k < kWords; ++k) {
-                    x[k] = p0[32 * k];
-                    y[k] = p1[32 * k];
+                    xa[k] = xb[k];
+                    ya[k] = yb[k];
                 }
+            }
 #pragma unroll
-                for (int k = 0; k < kWords; ++k) {
-                    if (ELEM == 1) {
-                        L1[j][k] = L1[j][k] + x[k] + y[k];
-                        L2[j][k] = imad_acc(prmt(x[k], 0u, 0x4341u), one, L2[j][k]);
-                        L2[j][k] = imad_acc(prmt(y[k], 0u, 0x4341u), one, L2[j][k]);
-                    } else if (ELEM == 2) {
-                        P[j][k][0] = add_f16_lo(y[k], add_f16_lo(x[k], P[j][k][0]));
-                        P[j][k][SPW - 1] = add_f16_hi(y[k], add_f16_hi(x[k], P[j][k][SPW - 1]));
-                    } else {
-                        P[j][k][0] = __fadd_rn(__fadd_rn(P[j][k][0], __uint_as_float(x[k])),
-                                               __uint_as_float(y[k]));
-                    }
-                }
+            for (int j = 0; j < DT; ++j) {
+                A0[j] = B0[j];
+                A1[j] = B1[j];
             }
         }
         __syncwarp();

@@ -65,7 +65,7 @@ std::vector<dd_tiles> auto_tiles(dd_dtype t) {
     for (int dcta = base.dm_per_thread * base.dm_warps; dcta >= 1; dcta /= 2) {
         const int dthr = std::min(base.dm_per_thread, dcta);
         const int wd = dcta / dthr;
-        const int wt = std::max(1, std::min(kMaxConsumerWarps / wd, max_t_cta / warp_span(t)));
+        const int wt = std::max(1, std::min(max_consumer_warps(dthr) / wd, max_t_cta / warp_span(t)));
         for (int cs = base.chan_per_stage; cs >= 2; cs /= 2)
             out.push_back(dd_tiles{dthr, wd, wt, cs});
     }
@@ -78,9 +78,9 @@ dd_status make_geometry(dd_plan_s *p, dd_dtype t, const dd_tiles &tl, Geometry *
     const int dthr = tl.dm_per_thread;
     bool ok_dthr = dthr == 1 || dthr == 2 || dthr == 4;
     if (!ok_dthr || tl.dm_warps < 1 || tl.time_warps < 1 ||
-        tl.dm_warps * tl.time_warps > kMaxConsumerWarps)
+        tl.dm_warps * tl.time_warps > max_consumer_warps(dthr))
         return fail(DD_ERR_INVALID, "tile shape: dm_per_thread must be 1, 2 or 4 and "
-                                    "dm_warps*time_warps in 1..12");
+                                    "dm_warps*time_warps in 1..16 (1..12 with 4 DMs per thread)");
     if (tl.chan_per_stage < 2 || tl.chan_per_stage > 64 || (tl.chan_per_stage & 1))
         return fail(DD_ERR_INVALID, "tile shape: chan_per_stage must be even, 2..64");
     const int limit = (t == DD_U8) ? kSwarChannels : kFloatBlock;
@@ -114,9 +114,11 @@ dd_status make_geometry(dd_plan_s *p, dd_dtype t, const dd_tiles &tl, Geometry *
     }
     const int64_t wp = widest + 16;
     const int64_t zero_bytes = ((int64_t)r.elem * r.t_cta + 16 + 15) / 16 * 16;
+    // Per stage: the staged rows (every byte phase) and the producer's
+    // offset table (one int per staged row and DM of the CTA).
     auto smem_for = [&](int64_t n) {
-        return n * tl.chan_per_stage * r.nph * wp + n * tl.chan_per_stage * 16 + zero_bytes +
-               16 * n;
+        const int64_t table = (n * tl.chan_per_stage * r.dm_cta * 4 + 15) / 16 * 16;
+        return n * tl.chan_per_stage * r.nph * wp + table + zero_bytes + 16 * n;
     };
     int nst = 4;
     while (nst > 2 && smem_for(nst) > kMaxSmem)

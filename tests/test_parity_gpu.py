@@ -259,3 +259,19 @@ def test_launch_count_and_status(dd):
     plan.execute(x, out)
     plan.sync()
     assert dd.launch_count() == n0 + 2  # phase planes + de-dispersion
+
+
+def test_autotuner_picks_a_shape_that_stays_bit_exact(dd, oracle_lib):
+    rng = np.random.default_rng(31)
+    band, table, dms, nin, data = _random_case(rng, 200, 70, 3000, "u8", sorted_dms=True)
+    plan = dd.Plan(200, *band, dms)
+    x = _dev(data)
+    out = torch.empty((70, 3000), dtype=torch.float32, device="cuda")
+    res = plan.autotune(x, out, nsamp_in=nin, reps=1)
+    timed = [r for r in res if r[1] >= 0]
+    assert len(timed) >= 3
+    best = min(timed, key=lambda r: r[1])[0]
+    assert plan.get_tiles("u8") == best
+    got = _run(dd, plan, data, nin, 3000)
+    want = oracle_lib.dedisperse(np.ascontiguousarray(data[:, :nin]), table, dms, 3000)
+    assert np.array_equal(got, want)
