@@ -164,23 +164,29 @@ __device__ __forceinline__ void record(int *status, int code) {
     atomicCAS(status, kDevOk, code);
 }
 
+// Store (first widening of a uint8 SWAR block) or add (later blocks) four
+// exact integer sums to out[t..t+3].  Later blocks use fire-and-forget
+// vector reductions: the values are integers below 2^24, so FP32 addition is
+// exact in any order and the thread does not wait for the old values.
 __device__ __forceinline__ void store4(float *row, int64_t t, int64_t n, float4 v,
                                        bool accumulate) {
     if (t + 3 < n) {
         float4 *p = reinterpret_cast<float4 *>(row + t);
-        if (accumulate) {
-            const float4 o = *p;
-            v.x += o.x;
-            v.y += o.y;
-            v.z += o.z;
-            v.w += o.w;
-        }
-        *p = v;
+        if (accumulate)
+            asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(v.x),
+                         "f"(v.y), "f"(v.z), "f"(v.w)
+                         : "memory");
+        else
+            *p = v;
     } else {
         const float e[4] = {v.x, v.y, v.z, v.w};
         for (int i = 0; i < 4; ++i)
-            if (t + i < n)
-                row[t + i] = accumulate ? row[t + i] + e[i] : e[i];
+            if (t + i < n) {
+                if (accumulate)
+                    atomicAdd(row + t + i, e[i]);
+                else
+                    row[t + i] = e[i];
+            }
     }
 }
 
@@ -331,7 +337,9 @@ __global__ void __launch_bounds__(32 * (max_consumer_warps(DT) + 1), 1)
                     const int k = lane + 32 * h;
                     if (k < dm_cta) {
                         const int s = shift_of(dmk[h], ds);
-                        tab[r * dm_cta + k] = base + ELEM * s + (s & (NPH - 1)) * (wp - ELEM);
+                        // pair layout: [r/2][k][r%2], so one LDS.64 gives both rows
+                        tab[((r >> 1) * dm_cta + k) * 2 + (r & 1)] =
+                            base + ELEM * s + (s & (NPH - 1)) * (wp - ELEM);
                     }
                 }
             }
@@ -441,38 +449,18 @@ __global__ void __launch_bounds__(32 * (max_consumer_warps(DT) + 1), 1)
                 }
     };
 
-    // Offsets of this thread's DT DMs in rows 2q and 2q+1 of stage buffer b.
-    auto pair_offsets = [&](int b, int q, int (&o0)[DT], int (&o1)[DT]) {
-        const int *r0 = atab + b * tab_stride + (2 * q) * dm_cta + kw;
-        const int *r1 = r0 + dm_cta;
-        if (DT == 4) {
-            const int4 u = *reinterpret_cast<const int4 *>(r0);
-            const int4 v = *reinterpret_cast<const int4 *>(r1);
-            o0[0] = u.x; o0[DT > 1 ? 1 : 0] = u.y; o0[DT > 2 ? 2 : 0] = u.z; o0[DT > 3 ? 3 : 0] = u.w;
-            o1[0] = v.x; o1[DT > 1 ? 1 : 0] = v.y; o1[DT > 2 ? 2 : 0] = v.z; o1[DT > 3 ? 3 : 0] = v.w;
-        } else if (DT == 2) {
-            const int2 u = *reinterpret_cast<const int2 *>(r0);
-            const int2 v = *reinterpret_cast<const int2 *>(r1);
-            o0[0] = u.x; o0[DT > 1 ? 1 : 0] = u.y;
-            o1[0] = v.x; o1[DT > 1 ? 1 : 0] = v.y;
-        } else {
-            o0[0] = r0[0];
-            o1[0] = r1[0];
-        }
-#pragma unroll
-        for (int j = 0; j < DT; ++j) {
-            o0[j] += thr_off;
-            o1[j] += thr_off;
-        }
-    };
-    auto load_words = [&](int off0, int off1, uint32_t (&x)[kWords], uint32_t (&y)[kWords]) {
-        const uint32_t *p0 = reinterpret_cast<const uint32_t *>(smem + off0);
-        const uint32_t *p1 = reinterpret_cast<const uint32_t *>(smem + off1);
+    auto load_words = [&](int2 off, uint32_t (&x)[kWords], uint32_t (&y)[kWords]) {
+        const uint32_t *p0 = reinterpret_cast<const uint32_t *>(smem + off.x + thr_off);
+        const uint32_t *p1 = reinterpret_cast<const uint32_t *>(smem + off.y + thr_off);
 #pragma unroll
         for (int k = 0; k < kWords; ++k) {
             x[k] = p0[32 * k];
             y[k] = p1[32 * k];
         }
+    };
+    // Offsets of rows 2q, 2q+1 of stage buffer b for this thread's DM j.
+    auto offsets = [&](int b, int q, int j) {
+        return *reinterpret_cast<const int2 *>(atab + b * tab_stride + (q * dm_cta + kw + j) * 2);
     };
     auto accumulate = [&](int j, const uint32_t (&x)[kWords], const uint32_t (&y)[kWords]) {
 #pragma unroll
@@ -491,16 +479,18 @@ __global__ void __launch_bounds__(32 * (max_consumer_warps(DT) + 1), 1)
         }
     };
 
-    const int npairs = cstage / 2;
-    int A0[DT], A1[DT], B0[DT], B1[DT];
+    // Iterations (channel pair q, DM j) run in order; the words of the next
+    // iteration are loaded into the other register buffer before the current
+    // ones are summed.  The pair loop is unrolled by two, so the buffers
+    // alternate with the (compile-time) parity of the iteration.
+    const int npairs = cstage / 2;  // even: chan_per_stage is a multiple of 4
     uint32_t xa[kWords], ya[kWords], xb[kWords], yb[kWords];
     if (nstage > 0) {
         if (!mbar_wait(full0, 0)) {
             record(a.status, kDevTimeout);
             return;
         }
-        pair_offsets(0, 0, A0, A1);
-        load_words(A0[0], A1[0], xa, ya);
+        load_words(offsets(0, 0, 0), xa, ya);
     }
     for (int st = 0; st < nstage; ++st) {
         const int b = st % nst;
@@ -512,44 +502,27 @@ __global__ void __launch_bounds__(32 * (max_consumer_warps(DT) + 1), 1)
             since_flush = 0;
         }
         since_flush += cstage;
-        for (int q = 0; q < npairs; ++q) {
-            bool have_next = true;
-            if (q + 1 < npairs) {
-                pair_offsets(b, q + 1, B0, B1);
-            } else if (st + 1 < nstage) {
-                const int bn = (st + 1) % nst;
-                if (!mbar_wait(full0 + 8 * bn, ((st + 1) / nst) & 1)) {
-                    record(a.status, kDevTimeout);
-                    return;
-                }
-                pair_offsets(bn, 0, B0, B1);
-            } else {
-                have_next = false;
-            }
+        for (int q = 0; q < npairs; q += 2) {
 #pragma unroll
-            for (int j = 0; j < DT; ++j) {
-                // Alternate register buffers: even j reads (xa,ya), odd j (xb,yb).
-                uint32_t (&cx)[kWords] = (j & 1) ? xb : xa;
-                uint32_t (&cy)[kWords] = (j & 1) ? yb : ya;
-                uint32_t (&nx)[kWords] = (j & 1) ? xa : xb;
-                uint32_t (&ny)[kWords] = (j & 1) ? ya : yb;
-                if (j + 1 < DT)
-                    load_words(A0[j + 1 < DT ? j + 1 : 0], A1[j + 1 < DT ? j + 1 : 0], nx, ny);
-                else if (have_next)
-                    load_words(B0[0], B1[0], nx, ny);
+            for (int i = 0; i < 2 * DT; ++i) {
+                uint32_t (&cx)[kWords] = (i & 1) ? xb : xa;
+                uint32_t (&cy)[kWords] = (i & 1) ? yb : ya;
+                uint32_t (&nx)[kWords] = (i & 1) ? xa : xb;
+                uint32_t (&ny)[kWords] = (i & 1) ? ya : yb;
+                const int j = i % DT;
+                if (i + 1 < 2 * DT) {
+                    load_words(offsets(b, q + (i + 1) / DT, (i + 1) % DT), nx, ny);
+                } else if (q + 2 < npairs) {
+                    load_words(offsets(b, q + 2, 0), nx, ny);
+                } else if (st + 1 < nstage) {
+                    const int bn = (st + 1) % nst;
+                    if (!mbar_wait(full0 + 8 * bn, ((st + 1) / nst) & 1)) {
+                        record(a.status, kDevTimeout);
+                        return;
+                    }
+                    load_words(offsets(bn, 0, 0), nx, ny);
+                }
                 accumulate(j, cx, cy);
-            }
-            if (DT & 1) {  // odd DT: the next words landed in (xb,yb)
-#pragma unroll
-                for (int k = 0; k < kWords; ++k) {
-                    xa[k] = xb[k];
-                    ya[k] = yb[k];
-                }
-            }
-#pragma unroll
-            for (int j = 0; j < DT; ++j) {
-                A0[j] = B0[j];
-                A1[j] = B1[j];
             }
         }
         __syncwarp();

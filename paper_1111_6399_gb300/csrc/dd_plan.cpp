@@ -66,7 +66,7 @@ std::vector<dd_tiles> auto_tiles(dd_dtype t) {
         const int dthr = std::min(base.dm_per_thread, dcta);
         const int wd = dcta / dthr;
         const int wt = std::max(1, std::min(max_consumer_warps(dthr) / wd, max_t_cta / warp_span(t)));
-        for (int cs = base.chan_per_stage; cs >= 2; cs /= 2)
+        for (int cs = base.chan_per_stage; cs >= 4; cs /= 2)
             out.push_back(dd_tiles{dthr, wd, wt, cs});
     }
     return out;
@@ -81,8 +81,8 @@ dd_status make_geometry(dd_plan_s *p, dd_dtype t, const dd_tiles &tl, Geometry *
         tl.dm_warps * tl.time_warps > max_consumer_warps(dthr))
         return fail(DD_ERR_INVALID, "tile shape: dm_per_thread must be 1, 2 or 4 and "
                                     "dm_warps*time_warps in 1..16 (1..12 with 4 DMs per thread)");
-    if (tl.chan_per_stage < 2 || tl.chan_per_stage > 64 || (tl.chan_per_stage & 1))
-        return fail(DD_ERR_INVALID, "tile shape: chan_per_stage must be even, 2..64");
+    if (tl.chan_per_stage < 4 || tl.chan_per_stage > 64 || (tl.chan_per_stage & 3))
+        return fail(DD_ERR_INVALID, "tile shape: chan_per_stage must be a multiple of 4, 4..64");
     const int limit = (t == DD_U8) ? kSwarChannels : kFloatBlock;
     if (limit % tl.chan_per_stage != 0)
         return fail(DD_ERR_INVALID, "tile shape: chan_per_stage must divide the "

@@ -82,7 +82,7 @@ def test_tile_validation(dd):
     assert p.get_tiles("u8") == (4, 12, 1, 8)
     p.set_tiles("u8", 2, 6, 2, 4)
     assert p.get_tiles("u8") == (2, 6, 2, 4)
-    for bad in [(3, 8, 1, 8), (4, 16, 1, 8), (4, 8, 1, 7), (4, 8, 1, 0), (1, 1, 1, 96),
+    for bad in [(3, 8, 1, 8), (4, 16, 1, 8), (4, 8, 1, 7), (4, 8, 1, 6), (4, 8, 1, 0), (1, 1, 1, 96),
                 (4, 12, 1, 64)]:   # the last needs more shared memory than a CTA has
         with pytest.raises(dd.DDError):
             p.set_tiles("u8", *bad)

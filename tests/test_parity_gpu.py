@@ -82,8 +82,8 @@ def test_small_workload_bit_exact(dd, oracle_lib):
     assert np.array_equal(got, want)
 
 
-TILES_U8 = [(4, 12, 1, 8), (4, 4, 2, 8), (2, 3, 1, 2), (1, 1, 1, 16), (4, 5, 2, 4),
-            (2, 8, 1, 32), (1, 12, 1, 64), (4, 6, 1, 2)]
+TILES_U8 = [(4, 12, 1, 8), (4, 4, 2, 8), (2, 3, 1, 4), (1, 1, 1, 16), (4, 5, 2, 4),
+            (2, 8, 1, 32), (1, 12, 1, 64), (4, 6, 1, 4), (2, 16, 1, 8), (1, 16, 1, 4)]
 
 
 @pytest.mark.parametrize("tiles", TILES_U8)
@@ -116,7 +116,7 @@ def test_float_fuzz(dd, oracle_lib, kind, seed):
     band, table, dms, nin, data = _random_case(rng, nchan, ndm, nsamp_out, kind)
     plan = dd.Plan(nchan, *band, dms)
     if seed == 2:
-        plan.set_tiles(kind[:3], 1, 3, 2, 2)
+        plan.set_tiles(kind[:3], 1, 3, 2, 4)
     got = _run(dd, plan, data, nin, nsamp_out)
     want, asum = oracle_lib.dedisperse(np.ascontiguousarray(data[:, :nin]), table, dms,
                                        nsamp_out, with_abssum=True)
