@@ -296,7 +296,9 @@ def run_ours(args, w):
                      "unit": "Tadd/s", "frac": achieved / peak_adds, "traffic": None,
                      "peak_source": f"{SM_COUNT} SMs x {ADD_LANES_PER_SM} lanes x "
                                     f"{pk.get('sm_max_mhz', 2070.0):.0f} MHz ({pk_kind} max clock)",
-                     "kernel": "dedisperse_kernel<1,4>", "kernel_ms": kernel_ms,
+                     "kernel": "dedisperse_kernel<1,%d,%d>" % (plan.get_tiles("u8")[0],
+                                                                 plan.get_tiles("u8")[4]),
+                     "kernel_ms": kernel_ms,
                      "step_ms": step_ms},
         "real_time_factor": w.duration_s() / (step_ms / 1e3),
         "e2e": {"value": adds * world / e2e_s, "unit": UNIT,

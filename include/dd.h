@@ -72,17 +72,21 @@ typedef struct dd_plan_s *dd_plan_t;
 /* Tile shape of the de-dispersion kernel (chosen by the plan or the autotuner).
  *   dm_per_thread    trial DMs each thread accumulates (register accumulators)
  *   dm_warps         warps of a CTA along the DM axis
- *   time_warps       warps of a CTA along the time axis (dm_warps*time_warps <= 16,
- *                    <= 12 with 4 DMs per thread; the CTA has one more warp
- *                    that stages the data)
+ *   time_warps       warps of a CTA along the time axis
  *   chan_per_stage   channels staged in shared memory per pipeline stage
+ *                    (a multiple of 4, 4..64)
+ *   words_per_thread 4-byte words of output time per DM and thread: 4 or 8
  * A CTA covers dm_per_thread*dm_warps DMs and time_warps*span samples, where
- * span = 1024 (uint8), 512 (FP16) or 256 (FP32) samples per warp. */
+ * span = 32*words_per_thread*(4/element size) samples per warp (1024 for
+ * uint8 with 8 words).  Warp limits (dm_warps*time_warps) by register need:
+ * 12 for 4 DMs x 8 words, 16 for 2x8, 20 for 1x8 and 4x4, 24 for 2x4 and 1x4;
+ * the CTA has one more warp that stages the data. */
 typedef struct dd_tiles {
     int dm_per_thread;
     int dm_warps;
     int time_warps;
     int chan_per_stage;
+    int words_per_thread;
 } dd_tiles;
 
 /* --- plan (Sec. 2: the dispersion law and the trial-DM grid) ------------- */

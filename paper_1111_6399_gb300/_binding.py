@@ -38,10 +38,12 @@ class DDError(RuntimeError):
 
 class Tiles(ctypes.Structure):
     _fields_ = [("dm_per_thread", ctypes.c_int), ("dm_warps", ctypes.c_int),
-                ("time_warps", ctypes.c_int), ("chan_per_stage", ctypes.c_int)]
+                ("time_warps", ctypes.c_int), ("chan_per_stage", ctypes.c_int),
+                ("words_per_thread", ctypes.c_int)]
 
     def as_tuple(self):
-        return (self.dm_per_thread, self.dm_warps, self.time_warps, self.chan_per_stage)
+        return (self.dm_per_thread, self.dm_warps, self.time_warps, self.chan_per_stage,
+                self.words_per_thread)
 
 
 class TuneResult(ctypes.Structure):
@@ -103,8 +105,8 @@ def elem_size(code: int) -> int:
     return (1, 2, 4)[code]
 
 
-def warp_span(code: int) -> int:
-    return (1024, 512, 256)[code]
+def warp_span(code: int, words: int = 8) -> int:
+    return 32 * words * (4 // (1, 2, 4)[code])
 
 
 def launch_count() -> int:
@@ -166,8 +168,9 @@ class Plan:
         check(lib.dd_plan_get_tiles(self.handle, dtype_code(dtype), ctypes.byref(t)))
         return t.as_tuple()
 
-    def set_tiles(self, dtype, dm_per_thread, dm_warps, time_warps, chan_per_stage):
-        t = Tiles(dm_per_thread, dm_warps, time_warps, chan_per_stage)
+    def set_tiles(self, dtype, dm_per_thread, dm_warps, time_warps, chan_per_stage,
+                  words_per_thread=8):
+        t = Tiles(dm_per_thread, dm_warps, time_warps, chan_per_stage, words_per_thread)
         check(lib.dd_plan_set_tiles(self.handle, dtype_code(dtype), ctypes.byref(t)))
 
     # -- execution --------------------------------------------------------

@@ -252,21 +252,24 @@ extern "C" dd_status dd_execute_host(dd_plan_t p, const void *in_host, dd_dtype 
 static std::vector<dd_tiles> tune_candidates(dd_dtype t) {
     std::vector<dd_tiles> out;
     const int dthrs[3] = {1, 2, 4};
-    const int dws[6] = {4, 6, 8, 12, 16, 2};
+    const int nws[2] = {8, 4};
+    const int dws[8] = {4, 6, 8, 10, 12, 16, 20, 24};
     const int wts[3] = {1, 2, 4};
-    const int css[4] = {4, 8, 16, 32};
-    for (int dthr : dthrs)
-        for (int dw : dws)
-            for (int wt : wts) {
-                if (dw * wt > dd::max_consumer_warps(dthr) || dw * wt < 4)
-                    continue;
-                for (int cs : css) {
-                    const int limit = t == DD_U8 ? dd::kSwarChannels : dd::kFloatBlock;
-                    if (limit % cs != 0)
+    const int css[3] = {4, 8, 16};
+    for (int nw : nws)
+        for (int dthr : dthrs)
+            for (int dw : dws)
+                for (int wt : wts) {
+                    const int w = dw * wt;
+                    if (w > dd::max_consumer_warps(dthr, nw) || w < 8)
                         continue;
-                    out.push_back(dd_tiles{dthr, dw, wt, cs});
+                    for (int cs : css) {
+                        const int limit = t == DD_U8 ? dd::kSwarChannels : dd::kFloatBlock;
+                        if (limit % cs != 0)
+                            continue;
+                        out.push_back(dd_tiles{dthr, dw, wt, cs, nw});
+                    }
                 }
-            }
     return out;
 }
 

@@ -12,11 +12,10 @@
 
 namespace dd {
 
-// Samples covered by one warp along time: 32 lanes x kWords 4-byte words x
+// Samples covered by one warp along time: 32 lanes x `words` 4-byte words x
 // (4 / element size) samples per word.
-constexpr int kWords = 8;
 inline int elem_size(dd_dtype t) { return t == DD_U8 ? 1 : (t == DD_F16 ? 2 : 4); }
-inline int warp_span(dd_dtype t) { return 32 * kWords * (4 / elem_size(t)); }
+inline int warp_span(dd_dtype t, int words) { return 32 * words * (4 / elem_size(t)); }
 inline int phases(dd_dtype t) { return 4 / elem_size(t); }
 
 // Channels summed into 16-bit SWAR lanes before they are widened (uint8):
@@ -26,17 +25,18 @@ constexpr int kSwarChannels = 256;
 constexpr int kFloatBlock = 64;
 
 constexpr int kMaxSmem = 232448;  // 227 KB dynamic shared memory per CTA
-// Consumer warps per CTA (plus one producer warp).  With 4 DMs per thread
-// the accumulators need ~128 registers, so 12 + 1 warps (at most 4 per SM
-// sub-partition); with 1-2 DMs per thread 16 + 1 warps fit in 96 registers.
-constexpr int kMaxConsumerWarps = 16;
+// Consumer warps per CTA (plus one producer warp), from the registers a
+// thread needs: accumulators 2*DT*NW (uint8) + two load buffers 4*NW + ~24.
+// 13 warps leave 128 registers a thread (at most 4 warps per SM
+// sub-partition), 17 leave 96, 21 leave 85, 25 leave 73.
 #ifdef __CUDACC__
 #define DD_HD __host__ __device__
 #else
 #define DD_HD
 #endif
-DD_HD constexpr int max_consumer_warps(int dm_per_thread) {
-    return dm_per_thread >= 4 ? 12 : 16;
+DD_HD constexpr int max_consumer_warps(int dm_per_thread, int words) {
+    return words >= 8 ? (dm_per_thread >= 4 ? 12 : dm_per_thread == 2 ? 16 : 20)
+                      : (dm_per_thread >= 4 ? 20 : 24);
 }
 
 // Device status word values (written by kernels, read by dd_sync).

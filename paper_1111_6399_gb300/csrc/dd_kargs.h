@@ -1,0 +1,48 @@
+// Kernel arguments of the de-dispersion kernel and the per-element-size
+// launchers (one translation unit each: dd_kernel_u8.cu, _f16.cu, _f32.cu).
+#pragma once
+
+#include <cuda_runtime_api.h>
+
+#include <cstdint>
+
+namespace dd {
+
+struct KArgs {
+    const uint8_t *in;
+    const uint8_t *planes;  // byte-phase planes 1..NPH-1 (NULL for FP32)
+    int64_t plane_stride;   // bytes between planes
+    int64_t in_pitch_b;     // bytes between channel rows
+    int64_t nsamp_in;       // valid samples per row
+    float *out;
+    int64_t out_pitch;      // floats between DM rows
+    int64_t nsamp_out;
+    const float *dmshift;
+    const float *dm_sorted;
+    const int *perm;
+    int nchan;
+    int dm_warps;
+    int time_warps;
+    int ntile_d;
+    int cstage;
+    int nstages;
+    int wp;                 // bytes per phase row
+    int zero_bytes;         // bytes of the zero row (padding channels)
+    uint32_t one;           // the constant 1, opaque to the compiler
+    int *status;
+};
+
+// Launch dedisperse_kernel<elem, dthr, nw> with `threads` threads per CTA.
+cudaError_t launch_kernel_u8(const KArgs &a, unsigned grid, int threads, int smem,
+                             cudaStream_t s, int dthr, int nw);
+cudaError_t launch_kernel_f16(const KArgs &a, unsigned grid, int threads, int smem,
+                              cudaStream_t s, int dthr, int nw);
+cudaError_t launch_kernel_f32(const KArgs &a, unsigned grid, int threads, int smem,
+                              cudaStream_t s, int dthr, int nw);
+// Byte-phase planes of an 8- or 16-bit input (pre-pass).
+cudaError_t launch_planes_u8(const uint8_t *in, int64_t pitch_b, int nchan, int64_t nsamp_in,
+                             uint8_t *planes, int64_t plane_stride, cudaStream_t s);
+cudaError_t launch_planes_f16(const uint8_t *in, int64_t pitch_b, int nchan, int64_t nsamp_in,
+                              uint8_t *planes, int64_t plane_stride, cudaStream_t s);
+
+}  // namespace dd

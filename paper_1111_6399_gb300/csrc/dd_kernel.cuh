@@ -1,3 +1,4 @@
+#pragma once
 // Brute-force incoherent de-dispersion kernels for sm_103a (GB300).
 //
 //   out[d][t] = sum_c in[c][t + s(c,d)],   s(c,d) = trunc(dm[d] * dmshift[c])
@@ -38,6 +39,7 @@
 #include <algorithm>
 #include <cstdint>
 
+#include "dd_kargs.h"
 #include "dd_internal.h"
 
 namespace dd {
@@ -45,29 +47,6 @@ namespace {
 
 constexpr uint64_t kWaitLimitNs = 2000000000ull;  // 2 s
 
-struct KArgs {
-    const uint8_t *in;
-    const uint8_t *planes;  // byte-phase planes 1..NPH-1 (NULL for FP32)
-    int64_t plane_stride;   // bytes between planes
-    int64_t in_pitch_b;     // bytes between channel rows
-    int64_t nsamp_in;       // valid samples per row
-    float *out;
-    int64_t out_pitch;      // floats between DM rows
-    int64_t nsamp_out;
-    const float *dmshift;
-    const float *dm_sorted;
-    const int *perm;
-    int nchan;
-    int dm_warps;
-    int time_warps;
-    int ntile_d;
-    int cstage;
-    int nstages;
-    int wp;                 // bytes per phase row
-    int zero_bytes;         // bytes of the zero row (padding channels)
-    uint32_t one;           // the constant 1, opaque to the compiler
-    int *status;
-};
 
 
 __device__ __forceinline__ uint32_t smem_addr(const void *p) {
@@ -226,7 +205,7 @@ __global__ void __launch_bounds__(256) phase_planes_kernel(const uint8_t *__rest
 
 // ---------------------------------------------------------------------------
 // The de-dispersion kernel.  ELEM = bytes per sample (1, 2, 4); DT = DMs per
-// consumer thread.  Warps 0..ncw-1 consume, warp ncw produces.
+// consumer thread; NW = 4-byte words per DM per consumer thread (4 or 8).  Warps 0..ncw-1 consume, warp ncw produces.
 //
 // Per stage the producer also writes, for every staged channel row r and
 // every DM k of the CTA, the shared-memory byte offset of that DM's shifted
@@ -235,12 +214,12 @@ __global__ void __launch_bounds__(256) phase_planes_kernel(const uint8_t *__rest
 // software-pipeline: the 16 words of the next (channel pair, DM) are loaded
 // into the alternate register buffer before the current ones are summed.
 // ---------------------------------------------------------------------------
-template <int ELEM, int DT>
-__global__ void __launch_bounds__(32 * (max_consumer_warps(DT) + 1), 1)
+template <int ELEM, int DT, int NW>
+__global__ void __launch_bounds__(32 * (max_consumer_warps(DT, NW) + 1), 1)
     dedisperse_kernel(const KArgs a) {
     constexpr int NPH = 4 / ELEM;            // phase copies per row
     constexpr int SPW = 4 / ELEM;            // samples per 4-byte word
-    constexpr int SPAN = 32 * kWords * SPW;  // samples per warp
+    constexpr int SPAN = 32 * NW * SPW;  // samples per warp
     constexpr int FLUSH = (ELEM == 1) ? kSwarChannels : kFloatBlock;
 
     extern __shared__ __align__(128) uint8_t smem[];
@@ -388,12 +367,12 @@ __global__ void __launch_bounds__(32 * (max_consumer_warps(DT) + 1), 1)
     const int thr_off = ELEM * (wti * SPAN) + 4 * lane;
     const uint32_t one = a.one;
 
-    uint32_t L1[DT][kWords], L2[DT][kWords];                            // uint8 SWAR
-    float P[DT][kWords][SPW], S[DT][kWords][SPW], C[DT][kWords][SPW];  // floats
+    uint32_t L1[DT][NW], L2[DT][NW];                            // uint8 SWAR
+    float P[DT][NW][SPW], S[DT][NW][SPW], C[DT][NW][SPW];  // floats
 #pragma unroll
     for (int j = 0; j < DT; ++j)
 #pragma unroll
-        for (int k = 0; k < kWords; ++k) {
+        for (int k = 0; k < NW; ++k) {
             L1[j][k] = 0u;
             L2[j][k] = 0u;
 #pragma unroll
@@ -412,18 +391,23 @@ __global__ void __launch_bounds__(32 * (max_consumer_warps(DT) + 1), 1)
 #pragma unroll
         for (int j = 0; j < DT; ++j) {
             const int row = a.perm[kthr + j];
+            float *orow = a.out + (int64_t)row * a.out_pitch;
 #pragma unroll
-            for (int k = 0; k < kWords; ++k) {
+            for (int k = 0; k < NW; ++k) {
                 const uint32_t lo = L1[j][k] - (L2[j][k] << 8);
-                const float4 v = make_float4((float)(lo & 0xffffu), (float)(L2[j][k] & 0xffffu),
-                                             (float)(lo >> 16), (float)(L2[j][k] >> 16));
+                // Exact integer -> FP32 for values below 2^23 on the FMA pipe:
+                // the bits 0x4b000000 | v are the float 2^23 + v.
+                const float4 v = make_float4(
+                    __uint_as_float(0x4b000000u | (lo & 0xffffu)) - 8388608.0f,
+                    __uint_as_float(0x4b000000u | (L2[j][k] & 0xffffu)) - 8388608.0f,
+                    __uint_as_float(0x4b000000u | (lo >> 16)) - 8388608.0f,
+                    __uint_as_float(0x4b000000u | (L2[j][k] >> 16)) - 8388608.0f);
                 L1[j][k] = 0u;
                 L2[j][k] = 0u;
                 if (row >= 0) {
                     const int64_t t = tw + 4 * (lane + 32 * k);
                     if (t < a.nsamp_out)
-                        store4(a.out + (int64_t)row * a.out_pitch, t, a.nsamp_out, v,
-                               flushed_once);
+                        store4(orow, t, a.nsamp_out, v, flushed_once);
                 }
             }
         }
@@ -434,7 +418,7 @@ __global__ void __launch_bounds__(32 * (max_consumer_warps(DT) + 1), 1)
 #pragma unroll
         for (int j = 0; j < DT; ++j)
 #pragma unroll
-            for (int k = 0; k < kWords; ++k)
+            for (int k = 0; k < NW; ++k)
 #pragma unroll
                 for (int e = 0; e < SPW; ++e) {
                     // TwoSum(S, P): S + P = s + err exactly.
@@ -449,11 +433,11 @@ __global__ void __launch_bounds__(32 * (max_consumer_warps(DT) + 1), 1)
                 }
     };
 
-    auto load_words = [&](int2 off, uint32_t (&x)[kWords], uint32_t (&y)[kWords]) {
+    auto load_words = [&](int2 off, uint32_t (&x)[NW], uint32_t (&y)[NW]) {
         const uint32_t *p0 = reinterpret_cast<const uint32_t *>(smem + off.x + thr_off);
         const uint32_t *p1 = reinterpret_cast<const uint32_t *>(smem + off.y + thr_off);
 #pragma unroll
-        for (int k = 0; k < kWords; ++k) {
+        for (int k = 0; k < NW; ++k) {
             x[k] = p0[32 * k];
             y[k] = p1[32 * k];
         }
@@ -462,9 +446,9 @@ __global__ void __launch_bounds__(32 * (max_consumer_warps(DT) + 1), 1)
     auto offsets = [&](int b, int q, int j) {
         return *reinterpret_cast<const int2 *>(atab + b * tab_stride + (q * dm_cta + kw + j) * 2);
     };
-    auto accumulate = [&](int j, const uint32_t (&x)[kWords], const uint32_t (&y)[kWords]) {
+    auto accumulate = [&](int j, const uint32_t (&x)[NW], const uint32_t (&y)[NW]) {
 #pragma unroll
-        for (int k = 0; k < kWords; ++k) {
+        for (int k = 0; k < NW; ++k) {
             if (ELEM == 1) {
                 L1[j][k] = L1[j][k] + x[k] + y[k];
                 L2[j][k] = imad_acc(prmt(x[k], 0u, 0x4341u), one, L2[j][k]);
@@ -484,7 +468,7 @@ __global__ void __launch_bounds__(32 * (max_consumer_warps(DT) + 1), 1)
     // ones are summed.  The pair loop is unrolled by two, so the buffers
     // alternate with the (compile-time) parity of the iteration.
     const int npairs = cstage / 2;  // even: chan_per_stage is a multiple of 4
-    uint32_t xa[kWords], ya[kWords], xb[kWords], yb[kWords];
+    uint32_t xa[NW], ya[NW], xb[NW], yb[NW];
     if (nstage > 0) {
         if (!mbar_wait(full0, 0)) {
             record(a.status, kDevTimeout);
@@ -494,27 +478,25 @@ __global__ void __launch_bounds__(32 * (max_consumer_warps(DT) + 1), 1)
     }
     for (int st = 0; st < nstage; ++st) {
         const int b = st % nst;
-        if (since_flush + cstage > FLUSH) {
-            if (ELEM == 1)
-                flush_u8();
-            else
-                block_float();
-            since_flush = 0;
-        }
         since_flush += cstage;
+        // Widen (uint8) or close a compensated block (floats) after this stage
+        // if the next one would overflow it.  The next stage's first words are
+        // then loaded after the widening, so no prefetched buffer is live
+        // across it.
+        const bool widen = st + 1 < nstage && since_flush + cstage > FLUSH;
         for (int q = 0; q < npairs; q += 2) {
 #pragma unroll
             for (int i = 0; i < 2 * DT; ++i) {
-                uint32_t (&cx)[kWords] = (i & 1) ? xb : xa;
-                uint32_t (&cy)[kWords] = (i & 1) ? yb : ya;
-                uint32_t (&nx)[kWords] = (i & 1) ? xa : xb;
-                uint32_t (&ny)[kWords] = (i & 1) ? ya : yb;
+                uint32_t (&cx)[NW] = (i & 1) ? xb : xa;
+                uint32_t (&cy)[NW] = (i & 1) ? yb : ya;
+                uint32_t (&nx)[NW] = (i & 1) ? xa : xb;
+                uint32_t (&ny)[NW] = (i & 1) ? ya : yb;
                 const int j = i % DT;
                 if (i + 1 < 2 * DT) {
                     load_words(offsets(b, q + (i + 1) / DT, (i + 1) % DT), nx, ny);
                 } else if (q + 2 < npairs) {
                     load_words(offsets(b, q + 2, 0), nx, ny);
-                } else if (st + 1 < nstage) {
+                } else if (st + 1 < nstage && !widen) {
                     const int bn = (st + 1) % nst;
                     if (!mbar_wait(full0 + 8 * bn, ((st + 1) / nst) & 1)) {
                         record(a.status, kDevTimeout);
@@ -528,6 +510,19 @@ __global__ void __launch_bounds__(32 * (max_consumer_warps(DT) + 1), 1)
         __syncwarp();
         if (lane == 0)
             mbar_arrive(empty0 + 8 * b);
+        if (widen) {
+            if (ELEM == 1)
+                flush_u8();
+            else
+                block_float();
+            since_flush = 0;
+            const int bn = (st + 1) % nst;  // 2*DT iterations per pair step: next is xa/ya
+            if (!mbar_wait(full0 + 8 * bn, ((st + 1) / nst) & 1)) {
+                record(a.status, kDevTimeout);
+                return;
+            }
+            load_words(offsets(bn, 0, 0), xa, ya);
+        }
     }
 
     if (ELEM == 1) {
@@ -541,7 +536,7 @@ __global__ void __launch_bounds__(32 * (max_consumer_warps(DT) + 1), 1)
                 continue;
             float *orow = a.out + (int64_t)row * a.out_pitch;
 #pragma unroll
-            for (int k = 0; k < kWords; ++k) {
+            for (int k = 0; k < NW; ++k) {
                 const int64_t t = tw + SPW * (lane + 32 * k);
                 if (SPW == 1) {
                     if (t < a.nsamp_out)
@@ -560,19 +555,40 @@ __global__ void __launch_bounds__(32 * (max_consumer_warps(DT) + 1), 1)
     }
 }
 
-template <int ELEM, int DT>
-cudaError_t launch_t(const KArgs &a, const Geometry &g, int64_t ntiles, cudaStream_t s) {
-    auto k = dedisperse_kernel<ELEM, DT>;
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, g.smem);
+
+template <int ELEM, int DT, int NW>
+cudaError_t launch_one(const KArgs &a, unsigned grid, int threads, int smem, cudaStream_t s) {
+    auto k = dedisperse_kernel<ELEM, DT, NW>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess)
         return e;
-    k<<<(unsigned)ntiles, g.threads, g.smem, s>>>(a);
+    k<<<grid, threads, smem, s>>>(a);
     return cudaGetLastError();
 }
 
+// Instantiations for one element size: DMs per thread 1/2/4 x words 4/8.
 template <int ELEM>
-cudaError_t launch_planes(const uint8_t *in, int64_t pitch_b, int nchan, int64_t nsamp_in,
-                          uint8_t *planes, int64_t plane_stride, cudaStream_t s) {
+cudaError_t launch_elem(const KArgs &a, unsigned grid, int threads, int smem, cudaStream_t s,
+                        int dthr, int nw) {
+    if (nw == 4) {
+        switch (dthr) {
+        case 1: return launch_one<ELEM, 1, 4>(a, grid, threads, smem, s);
+        case 2: return launch_one<ELEM, 2, 4>(a, grid, threads, smem, s);
+        case 4: return launch_one<ELEM, 4, 4>(a, grid, threads, smem, s);
+        }
+    } else if (nw == 8) {
+        switch (dthr) {
+        case 1: return launch_one<ELEM, 1, 8>(a, grid, threads, smem, s);
+        case 2: return launch_one<ELEM, 2, 8>(a, grid, threads, smem, s);
+        case 4: return launch_one<ELEM, 4, 8>(a, grid, threads, smem, s);
+        }
+    }
+    return cudaErrorInvalidValue;
+}
+
+template <int ELEM>
+cudaError_t launch_planes_elem(const uint8_t *in, int64_t pitch_b, int nchan, int64_t nsamp_in,
+                               uint8_t *planes, int64_t plane_stride, cudaStream_t s) {
     const int64_t groups = (nsamp_in * ELEM + 15) / 16;
     const int64_t total = groups * nchan;
     const int64_t blocks = std::min<int64_t>((total + 255) / 256, 152 * 16);
@@ -581,90 +597,5 @@ cudaError_t launch_planes(const uint8_t *in, int64_t pitch_b, int nchan, int64_t
     return cudaGetLastError();
 }
 
-thread_local cudaEvent_t g_prof_start = nullptr;
-thread_local cudaEvent_t g_prof_stop = nullptr;
-
 }  // namespace
-
-int64_t scratch_bytes(dd_dtype dtype, int nchan, int64_t in_pitch_b) {
-    return (int64_t)(phases(dtype) - 1) * nchan * in_pitch_b;
-}
-
-dd_status launch_dedisperse(dd_plan_s *p, const Geometry &g, const DevTables &dt, const void *in,
-                            dd_dtype dtype, int64_t in_pitch, int64_t nsamp_in, float *out,
-                            int64_t out_pitch, int64_t nsamp_out, void *scratch, void *stream) {
-    if (nsamp_out == 0)
-        return DD_OK;
-    KArgs a;
-    a.in = static_cast<const uint8_t *>(in);
-    a.in_pitch_b = in_pitch * g.elem;
-    a.planes = static_cast<const uint8_t *>(scratch);
-    a.plane_stride = (int64_t)p->nchan * a.in_pitch_b;
-    a.nsamp_in = nsamp_in;
-    a.out = out;
-    a.out_pitch = out_pitch;
-    a.nsamp_out = nsamp_out;
-    a.dmshift = dt.dmshift;
-    a.dm_sorted = dt.dm_sorted;
-    a.perm = dt.perm;
-    a.nchan = p->nchan;
-    a.dm_warps = g.tiles.dm_warps;
-    a.time_warps = g.tiles.time_warps;
-    a.ntile_d = g.ntile_d;
-    a.cstage = g.tiles.chan_per_stage;
-    a.nstages = g.nstages;
-    a.wp = g.wp;
-    a.zero_bytes = g.zero_bytes;
-    a.one = 1u;
-    a.status = dt.status;
-    const int64_t ntile_t = (nsamp_out + g.t_cta - 1) / g.t_cta;
-    const int64_t ntiles = ntile_t * g.ntile_d;
-    if (ntiles > 0x7fffffffLL)
-        return fail(DD_ERR_INVALID, "too many tiles for one launch");
-    if (g.nph > 1 && scratch == nullptr)
-        return fail(DD_ERR_INVALID, "phase-plane scratch missing");
-    cudaStream_t s = static_cast<cudaStream_t>(stream);
-    cudaError_t e = cudaSuccess;
-    int launches = 1;
-    if (dtype == DD_U8) {
-        e = launch_planes<1>(a.in, a.in_pitch_b, p->nchan, nsamp_in, (uint8_t *)scratch,
-                             a.plane_stride, s);
-        ++launches;
-    } else if (dtype == DD_F16) {
-        e = launch_planes<2>(a.in, a.in_pitch_b, p->nchan, nsamp_in, (uint8_t *)scratch,
-                             a.plane_stride, s);
-        ++launches;
-    }
-    if (e != cudaSuccess)
-        return fail(DD_ERR_CUDA, std::string("phase-plane launch failed: ") + cudaGetErrorString(e));
-    const int dthr = g.tiles.dm_per_thread;
-    if (g_prof_start)
-        cudaEventRecord(g_prof_start, s);
-    switch (dtype) {
-    case DD_U8:
-        e = dthr == 1 ? launch_t<1, 1>(a, g, ntiles, s)
-          : dthr == 2 ? launch_t<1, 2>(a, g, ntiles, s) : launch_t<1, 4>(a, g, ntiles, s);
-        break;
-    case DD_F16:
-        e = dthr == 1 ? launch_t<2, 1>(a, g, ntiles, s)
-          : dthr == 2 ? launch_t<2, 2>(a, g, ntiles, s) : launch_t<2, 4>(a, g, ntiles, s);
-        break;
-    case DD_F32:
-        e = dthr == 1 ? launch_t<4, 1>(a, g, ntiles, s)
-          : dthr == 2 ? launch_t<4, 2>(a, g, ntiles, s) : launch_t<4, 4>(a, g, ntiles, s);
-        break;
-    }
-    if (e != cudaSuccess)
-        return fail(DD_ERR_CUDA, std::string("kernel launch failed: ") + cudaGetErrorString(e));
-    if (g_prof_stop)
-        cudaEventRecord(g_prof_stop, s);
-    count_launch(launches);
-    return DD_OK;
-}
-
 }  // namespace dd
-
-extern "C" void dd_profile_events(void *start_event, void *stop_event) {
-    dd::g_prof_start = static_cast<cudaEvent_t>(start_event);
-    dd::g_prof_stop = static_cast<cudaEvent_t>(stop_event);
-}

@@ -1,0 +1,91 @@
+// Host side of a de-dispersion launch: kernel arguments, the phase-plane
+// pre-pass, the per-dtype kernel dispatch and the profiling-event hook.
+#include <cuda_runtime_api.h>
+
+#include <string>
+
+#include "dd_internal.h"
+#include "dd_kargs.h"
+
+namespace dd {
+namespace {
+
+thread_local cudaEvent_t g_prof_start = nullptr;
+thread_local cudaEvent_t g_prof_stop = nullptr;
+
+}  // namespace
+
+int64_t scratch_bytes(dd_dtype dtype, int nchan, int64_t in_pitch_b) {
+    return (int64_t)(phases(dtype) - 1) * nchan * in_pitch_b;
+}
+
+dd_status launch_dedisperse(dd_plan_s *p, const Geometry &g, const DevTables &dt, const void *in,
+                            dd_dtype dtype, int64_t in_pitch, int64_t nsamp_in, float *out,
+                            int64_t out_pitch, int64_t nsamp_out, void *scratch, void *stream) {
+    if (nsamp_out == 0)
+        return DD_OK;
+    KArgs a;
+    a.in = static_cast<const uint8_t *>(in);
+    a.in_pitch_b = in_pitch * g.elem;
+    a.planes = static_cast<const uint8_t *>(scratch);
+    a.plane_stride = (int64_t)p->nchan * a.in_pitch_b;
+    a.nsamp_in = nsamp_in;
+    a.out = out;
+    a.out_pitch = out_pitch;
+    a.nsamp_out = nsamp_out;
+    a.dmshift = dt.dmshift;
+    a.dm_sorted = dt.dm_sorted;
+    a.perm = dt.perm;
+    a.nchan = p->nchan;
+    a.dm_warps = g.tiles.dm_warps;
+    a.time_warps = g.tiles.time_warps;
+    a.ntile_d = g.ntile_d;
+    a.cstage = g.tiles.chan_per_stage;
+    a.nstages = g.nstages;
+    a.wp = g.wp;
+    a.zero_bytes = g.zero_bytes;
+    a.one = 1u;
+    a.status = dt.status;
+    const int64_t ntile_t = (nsamp_out + g.t_cta - 1) / g.t_cta;
+    const int64_t ntiles = ntile_t * g.ntile_d;
+    if (ntiles > 0x7fffffffLL)
+        return fail(DD_ERR_INVALID, "too many tiles for one launch");
+    if (g.nph > 1 && scratch == nullptr)
+        return fail(DD_ERR_INVALID, "phase-plane scratch missing");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaSuccess;
+    int launches = 1;
+    if (dtype == DD_U8) {
+        e = launch_planes_u8(a.in, a.in_pitch_b, p->nchan, nsamp_in, (uint8_t *)scratch,
+                             a.plane_stride, s);
+        ++launches;
+    } else if (dtype == DD_F16) {
+        e = launch_planes_f16(a.in, a.in_pitch_b, p->nchan, nsamp_in, (uint8_t *)scratch,
+                              a.plane_stride, s);
+        ++launches;
+    }
+    if (e != cudaSuccess)
+        return fail(DD_ERR_CUDA, std::string("phase-plane launch failed: ") + cudaGetErrorString(e));
+    if (g_prof_start)
+        cudaEventRecord(g_prof_start, s);
+    const unsigned grid = (unsigned)ntiles;
+    const int dthr = g.tiles.dm_per_thread, nw = g.tiles.words_per_thread;
+    switch (dtype) {
+    case DD_U8: e = launch_kernel_u8(a, grid, g.threads, g.smem, s, dthr, nw); break;
+    case DD_F16: e = launch_kernel_f16(a, grid, g.threads, g.smem, s, dthr, nw); break;
+    case DD_F32: e = launch_kernel_f32(a, grid, g.threads, g.smem, s, dthr, nw); break;
+    }
+    if (e != cudaSuccess)
+        return fail(DD_ERR_CUDA, std::string("kernel launch failed: ") + cudaGetErrorString(e));
+    if (g_prof_stop)
+        cudaEventRecord(g_prof_stop, s);
+    count_launch(launches);
+    return DD_OK;
+}
+
+}  // namespace dd
+
+extern "C" void dd_profile_events(void *start_event, void *stop_event) {
+    dd::g_prof_start = static_cast<cudaEvent_t>(start_event);
+    dd::g_prof_stop = static_cast<cudaEvent_t>(stop_event);
+}

@@ -32,9 +32,9 @@ int trunc_product(float dm, float ds) {
 }
 
 uint64_t geo_key(dd_dtype t, const dd_tiles &tl) {
-    return ((uint64_t)t << 56) | ((uint64_t)tl.dm_per_thread << 42) |
-           ((uint64_t)tl.dm_warps << 28) | ((uint64_t)tl.time_warps << 14) |
-           (uint64_t)tl.chan_per_stage;
+    return ((uint64_t)t << 60) | ((uint64_t)tl.words_per_thread << 48) |
+           ((uint64_t)tl.dm_per_thread << 36) | ((uint64_t)tl.dm_warps << 24) |
+           ((uint64_t)tl.time_warps << 12) | (uint64_t)tl.chan_per_stage;
 }
 
 bool valid_dtype(dd_dtype t) { return t == DD_U8 || t == DD_F16 || t == DD_F32; }
@@ -52,9 +52,9 @@ void count_launch(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
 dd_tiles default_tiles(dd_dtype t) {
     switch (t) {
-    case DD_U8:  return dd_tiles{4, 12, 1, 8};
-    case DD_F16: return dd_tiles{1, 12, 1, 16};
-    default:     return dd_tiles{2, 12, 1, 16};
+    case DD_U8:  return dd_tiles{4, 12, 1, 8, 8};
+    case DD_F16: return dd_tiles{1, 12, 1, 16, 8};
+    default:     return dd_tiles{2, 12, 1, 16, 8};
     }
 }
 
@@ -65,9 +65,11 @@ std::vector<dd_tiles> auto_tiles(dd_dtype t) {
     for (int dcta = base.dm_per_thread * base.dm_warps; dcta >= 1; dcta /= 2) {
         const int dthr = std::min(base.dm_per_thread, dcta);
         const int wd = dcta / dthr;
-        const int wt = std::max(1, std::min(max_consumer_warps(dthr) / wd, max_t_cta / warp_span(t)));
+        const int nw = base.words_per_thread;
+        const int wt = std::max(1, std::min(max_consumer_warps(dthr, nw) / wd,
+                                            max_t_cta / warp_span(t, nw)));
         for (int cs = base.chan_per_stage; cs >= 4; cs /= 2)
-            out.push_back(dd_tiles{dthr, wd, wt, cs});
+            out.push_back(dd_tiles{dthr, wd, wt, cs, nw});
     }
     return out;
 }
@@ -76,11 +78,16 @@ dd_status make_geometry(dd_plan_s *p, dd_dtype t, const dd_tiles &tl, Geometry *
     if (!valid_dtype(t))
         return fail(DD_ERR_INVALID, "unknown dtype");
     const int dthr = tl.dm_per_thread;
+    const int nw = tl.words_per_thread;
     bool ok_dthr = dthr == 1 || dthr == 2 || dthr == 4;
-    if (!ok_dthr || tl.dm_warps < 1 || tl.time_warps < 1 ||
-        tl.dm_warps * tl.time_warps > max_consumer_warps(dthr))
+    if (!ok_dthr || (nw != 4 && nw != 8))
         return fail(DD_ERR_INVALID, "tile shape: dm_per_thread must be 1, 2 or 4 and "
-                                    "dm_warps*time_warps in 1..16 (1..12 with 4 DMs per thread)");
+                                    "words_per_thread 4 or 8");
+    if (tl.dm_warps < 1 || tl.time_warps < 1 ||
+        tl.dm_warps * tl.time_warps > max_consumer_warps(dthr, nw))
+        return fail(DD_ERR_INVALID, "tile shape: dm_warps*time_warps must be 1.." +
+                                        std::to_string(max_consumer_warps(dthr, nw)) +
+                                        " for this dm_per_thread and words_per_thread");
     if (tl.chan_per_stage < 4 || tl.chan_per_stage > 64 || (tl.chan_per_stage & 3))
         return fail(DD_ERR_INVALID, "tile shape: chan_per_stage must be a multiple of 4, 4..64");
     const int limit = (t == DD_U8) ? kSwarChannels : kFloatBlock;
@@ -91,7 +98,7 @@ dd_status make_geometry(dd_plan_s *p, dd_dtype t, const dd_tiles &tl, Geometry *
     r.tiles = tl;
     r.elem = elem_size(t);
     r.nph = phases(t);
-    r.span = warp_span(t);
+    r.span = warp_span(t, nw);
     r.dm_cta = dthr * tl.dm_warps;
     r.t_cta = r.span * tl.time_warps;
     r.threads = 32 * tl.dm_warps * tl.time_warps;

@@ -79,9 +79,9 @@ def test_invalid_plans_are_rejected(dd, args):
 def test_tile_validation(dd):
     w = fb.LBAND
     p = dd.Plan(w.nchan, w.fch1, w.foff, w.tsamp, w.dm_list())
-    assert p.get_tiles("u8") == (4, 12, 1, 8)
-    p.set_tiles("u8", 2, 6, 2, 4)
-    assert p.get_tiles("u8") == (2, 6, 2, 4)
+    assert p.get_tiles("u8") == (4, 12, 1, 8, 8)
+    p.set_tiles("u8", 2, 6, 2, 4, 4)
+    assert p.get_tiles("u8") == (2, 6, 2, 4, 4)
     for bad in [(3, 8, 1, 8), (4, 16, 1, 8), (4, 8, 1, 7), (4, 8, 1, 6), (4, 8, 1, 0), (1, 1, 1, 96),
                 (4, 12, 1, 64)]:   # the last needs more shared memory than a CTA has
         with pytest.raises(dd.DDError):

@@ -82,7 +82,7 @@ def test_small_workload_bit_exact(dd, oracle_lib):
     assert np.array_equal(got, want)
 
 
-TILES_U8 = [(4, 12, 1, 8), (4, 4, 2, 8), (2, 3, 1, 4), (1, 1, 1, 16), (4, 5, 2, 4),
+TILES_U8 = [(4, 12, 1, 8), (4, 4, 2, 8), (2, 3, 1, 4), (1, 1, 1, 16), (4, 5, 2, 4), (4, 10, 2, 8, 4), (2, 12, 2, 8, 4), (1, 24, 1, 4, 4),
             (2, 8, 1, 32), (1, 12, 1, 64), (4, 6, 1, 4), (2, 16, 1, 8), (1, 16, 1, 4)]
 
 
