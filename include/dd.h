@@ -80,7 +80,8 @@ typedef struct dd_plan_s *dd_plan_t;
  * span = 32*words_per_thread*(4/element size) samples per warp (1024 for
  * uint8 with 8 words).  Warp limits (dm_warps*time_warps) by register need:
  * 12 for 4 DMs x 8 words, 16 for 2x8, 20 for 1x8 and 4x4, 24 for 2x4 and 1x4;
- * the CTA has one more warp that stages the data. */
+ * the CTA has one more warp that stages the data.  At most 64 DMs per CTA
+ * (dm_per_thread*dm_warps <= 64). */
 typedef struct dd_tiles {
     int dm_per_thread;
     int dm_warps;

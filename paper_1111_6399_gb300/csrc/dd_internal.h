@@ -25,6 +25,7 @@ constexpr int kSwarChannels = 256;
 constexpr int kFloatBlock = 64;
 
 constexpr int kMaxSmem = 232448;  // 227 KB dynamic shared memory per CTA
+constexpr int kMaxDmPerCta = 64;   // DMs per CTA (offset-table columns, DM padding)
 // Consumer warps per CTA (plus one producer warp), from the registers a
 // thread needs: accumulators 2*DT*NW (uint8) + two load buffers 4*NW + ~24.
 // 13 warps leave 128 registers a thread (at most 4 warps per SM

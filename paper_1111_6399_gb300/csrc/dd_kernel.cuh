@@ -263,7 +263,7 @@ __global__ void __launch_bounds__(32 * (max_consumer_warps(DT, NW) + 1), 1)
         // ------------------------------ producer ------------------------------
         const float dm_min = a.dm_sorted[kcta];
         const float dm_max = a.dm_sorted[kcta + dm_cta - 1];
-        float dmk[2];
+        float dmk[2];  // DM columns lane and lane + 32 (dm_cta <= 64, host-checked)
         dmk[0] = a.dm_sorted[kcta + min(lane, dm_cta - 1)];
         dmk[1] = a.dm_sorted[kcta + min(lane + 32, dm_cta - 1)];
         int issued = 0;

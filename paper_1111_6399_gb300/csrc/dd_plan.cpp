@@ -94,6 +94,11 @@ dd_status make_geometry(dd_plan_s *p, dd_dtype t, const dd_tiles &tl, Geometry *
     if (limit % tl.chan_per_stage != 0)
         return fail(DD_ERR_INVALID, "tile shape: chan_per_stage must divide the "
                                     "accumulation block (256 for uint8, 64 otherwise)");
+    // The producer warp writes the offset table for DM columns lane and
+    // lane + 32, and the device DM list is padded by 64 entries: at most 64
+    // DMs per CTA.
+    if (dthr * tl.dm_warps > kMaxDmPerCta)
+        return fail(DD_ERR_INVALID, "tile shape: dm_per_thread*dm_warps must be <= 64");
     Geometry r;
     r.tiles = tl;
     r.elem = elem_size(t);

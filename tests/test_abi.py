@@ -83,7 +83,8 @@ def test_tile_validation(dd):
     p.set_tiles("u8", 2, 6, 2, 4, 4)
     assert p.get_tiles("u8") == (2, 6, 2, 4, 4)
     for bad in [(3, 8, 1, 8), (4, 16, 1, 8), (4, 8, 1, 7), (4, 8, 1, 6), (4, 8, 1, 0), (1, 1, 1, 96),
-                (4, 12, 1, 64)]:   # the last needs more shared memory than a CTA has
+                (4, 12, 1, 64),    # needs more shared memory than a CTA has
+                (4, 20, 1, 8, 4)]:  # 80 DMs per CTA (limit 64)
         with pytest.raises(dd.DDError):
             p.set_tiles("u8", *bad)
     with pytest.raises(dd.DDError):
