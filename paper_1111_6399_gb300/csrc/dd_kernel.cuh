@@ -68,6 +68,10 @@ __device__ __forceinline__ void mbar_expect_tx_arrive(uint32_t mb, uint32_t byte
                  : "memory");
 }
 
+__device__ __forceinline__ void mbar_expect_tx(uint32_t mb, uint32_t bytes) {
+    asm volatile("mbarrier.expect_tx.shared::cta.b64 [%0], %1;" ::"r"(mb), "r"(bytes) : "memory");
+}
+
 __device__ __forceinline__ void mbar_arrive(uint32_t mb) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(mb) : "memory");
 }
@@ -268,9 +272,22 @@ __global__ void __launch_bounds__(32 * (max_consumer_warps(DT, NW) + 1), 1)
         dmk[1] = a.dm_sorted[kcta + min(lane + 32, dm_cta - 1)];
         int issued = 0;
         bool ok = true;
+        // dmshift of the rows of the next stage (lane r: rows r and r + 32),
+        // loaded one stage ahead so the load latency overlaps the empty wait.
+        float ds_next[2];
+        for (int h = 0; h < 2; ++h) {
+            const int c = lane + 32 * h;
+            ds_next[h] = (lane + 32 * h < cstage && c < a.nchan) ? a.dmshift[c] : 0.0f;
+        }
         for (int st = 0; st < nstage; ++st) {
             const int b = st % nst;
             const int n = st / nst;
+            const float ds_cur[2] = {ds_next[0], ds_next[1]};
+            for (int h = 0; h < 2; ++h) {
+                const int c = (st + 1) * cstage + lane + 32 * h;
+                ds_next[h] = (st + 1 < nstage && lane + 32 * h < cstage && c < a.nchan)
+                                 ? a.dmshift[c] : 0.0f;
+            }
             if (n > 0 && !mbar_wait(empty0 + 8 * b, (n - 1) & 1)) {
                 ok = false;
                 break;
@@ -288,7 +305,7 @@ __global__ void __launch_bounds__(32 * (max_consumer_warps(DT, NW) + 1), 1)
                 const int c = st * cstage + r;
                 if (r >= cstage || c >= a.nchan)
                     continue;
-                const float ds = a.dmshift[c];
+                const float ds = ds_cur[h];
                 const int64_t smin = shift_of(dm_min, ds);
                 const int64_t smax = shift_of(dm_max, ds);
                 const int64_t first = (t0 + smin) & ~(int64_t)(16 / ELEM - 1);
@@ -307,6 +324,30 @@ __global__ void __launch_bounds__(32 * (max_consumer_warps(DT, NW) + 1), 1)
             }
             if (bad)
                 record(a.status, kDevCheck);
+            // Copies first: the expected byte count is registered without an
+            // arrival, the copies are issued, and the offset table is written
+            // while they are in flight; the arrival then releases the stage
+            // (the phase completes once it and every byte are in).
+            uint32_t total = (my_bytes[0] + my_bytes[1]) * NPH;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1)
+                total += __shfl_xor_sync(0xffffffffu, total, o);
+            if (lane == 0)
+                mbar_expect_tx(full0 + 8 * b, total);
+            __syncwarp();
+            for (int h = 0; h < 2; ++h) {
+                const int r = lane + 32 * h;
+                if (r >= cstage || my_bytes[h] == 0)
+                    continue;
+                const int c = st * cstage + r;
+                const int64_t off = (int64_t)c * a.in_pitch_b + my_first[h] * ELEM;
+                const uint32_t dst = smem_addr(buf + r * row_bytes);
+                bulk_g2s(dst, a.in + off, my_bytes[h], full0 + 8 * b);
+#pragma unroll
+                for (int p = 1; p < NPH; ++p)
+                    bulk_g2s(dst + p * wp, a.planes + (p - 1) * a.plane_stride + off, my_bytes[h],
+                             full0 + 8 * b);
+            }
             // Offset table: row r, DM k -> smem offset of the shifted window.
             for (int r = 0; r < cstage; ++r) {
                 const int base = __shfl_sync(0xffffffffu, my_base[r >> 5], r & 31);
@@ -322,27 +363,9 @@ __global__ void __launch_bounds__(32 * (max_consumer_warps(DT, NW) + 1), 1)
                     }
                 }
             }
-            uint32_t total = (my_bytes[0] + my_bytes[1]) * NPH;
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1)
-                total += __shfl_xor_sync(0xffffffffu, total, o);
             __syncwarp();
             if (lane == 0)
-                mbar_expect_tx_arrive(full0 + 8 * b, total);
-            __syncwarp();
-            for (int h = 0; h < 2; ++h) {
-                const int r = lane + 32 * h;
-                if (r >= cstage || my_bytes[h] == 0)
-                    continue;
-                const int c = st * cstage + r;
-                const int64_t off = (int64_t)c * a.in_pitch_b + my_first[h] * ELEM;
-                const uint32_t dst = smem_addr(buf + r * row_bytes);
-                bulk_g2s(dst, a.in + off, my_bytes[h], full0 + 8 * b);
-#pragma unroll
-                for (int p = 1; p < NPH; ++p)
-                    bulk_g2s(dst + p * wp, a.planes + (p - 1) * a.plane_stride + off, my_bytes[h],
-                             full0 + 8 * b);
-            }
+                mbar_arrive(full0 + 8 * b);
             issued = st + 1;
         }
         if (!ok)
