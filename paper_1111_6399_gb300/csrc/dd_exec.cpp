@@ -255,7 +255,7 @@ static std::vector<dd_tiles> tune_candidates(dd_dtype t) {
     const int nws[2] = {8, 4};
     const int dws[8] = {4, 6, 8, 10, 12, 16, 20, 24};
     const int wts[3] = {1, 2, 4};
-    const int css[3] = {4, 8, 16};
+    const int css[5] = {4, 8, 12, 16, 24};
     for (int nw : nws)
         for (int dthr : dthrs)
             for (int dw : dws)
@@ -265,7 +265,7 @@ static std::vector<dd_tiles> tune_candidates(dd_dtype t) {
                         continue;
                     for (int cs : css) {
                         const int limit = t == DD_U8 ? dd::kSwarChannels : dd::kFloatBlock;
-                        if (limit % cs != 0)
+                        if (cs > limit)
                             continue;
                         out.push_back(dd_tiles{dthr, dw, wt, cs, nw});
                     }

@@ -519,20 +519,24 @@ __global__ void __launch_bounds__(32 * (max_consumer_warps(DT, NW) + 1), 1)
                     load_words(offsets(b, q + (i + 1) / DT, (i + 1) % DT), nx, ny);
                 } else if (q + 2 < npairs) {
                     load_words(offsets(b, q + 2, 0), nx, ny);
-                } else if (st + 1 < nstage && !widen) {
-                    const int bn = (st + 1) % nst;
-                    if (!mbar_wait(full0 + 8 * bn, ((st + 1) / nst) & 1)) {
-                        record(a.status, kDevTimeout);
-                        return;
+                } else {
+                    // The words of this stage's last iteration are in registers:
+                    // release the stage before summing them.
+                    __syncwarp();
+                    if (lane == 0)
+                        mbar_arrive(empty0 + 8 * b);
+                    if (st + 1 < nstage && !widen) {
+                        const int bn = (st + 1) % nst;
+                        if (!mbar_wait(full0 + 8 * bn, ((st + 1) / nst) & 1)) {
+                            record(a.status, kDevTimeout);
+                            return;
+                        }
+                        load_words(offsets(bn, 0, 0), nx, ny);
                     }
-                    load_words(offsets(bn, 0, 0), nx, ny);
                 }
                 accumulate(j, cx, cy);
             }
         }
-        __syncwarp();
-        if (lane == 0)
-            mbar_arrive(empty0 + 8 * b);
         if (widen) {
             if (ELEM == 1)
                 flush_u8();

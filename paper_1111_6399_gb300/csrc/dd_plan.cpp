@@ -91,8 +91,8 @@ dd_status make_geometry(dd_plan_s *p, dd_dtype t, const dd_tiles &tl, Geometry *
     if (tl.chan_per_stage < 4 || tl.chan_per_stage > 64 || (tl.chan_per_stage & 3))
         return fail(DD_ERR_INVALID, "tile shape: chan_per_stage must be a multiple of 4, 4..64");
     const int limit = (t == DD_U8) ? kSwarChannels : kFloatBlock;
-    if (limit % tl.chan_per_stage != 0)
-        return fail(DD_ERR_INVALID, "tile shape: chan_per_stage must divide the "
+    if (tl.chan_per_stage > limit)
+        return fail(DD_ERR_INVALID, "tile shape: chan_per_stage must not exceed the "
                                     "accumulation block (256 for uint8, 64 otherwise)");
     // The producer warp writes the offset table for DM columns lane and
     // lane + 32, and the device DM list is padded by 64 entries: at most 64
