@@ -163,6 +163,30 @@ dd_status dd_execute_host(dd_plan_t plan, const void *in_host, dd_dtype dtype,
                           int64_t in_pitch, int64_t nsamp_in, float *out_host,
                           int64_t out_pitch, int64_t nsamp_out);
 
+/* De-disperse one beam like dd_execute, without allocating any device memory.
+ * The paper has no counterpart: this serves callers that cannot call
+ * cudaMalloc -- code running inside an allocator or memory-pool callback,
+ * real-time threads that must not take the driver's allocation locks, hosts
+ * that forbid the library from owning device memory.  Everything the kernels
+ * need beyond in and out (the plan's device tables, the status word, the
+ * byte-phase planes of 8/16-bit input) lives in one fixed 64 MiB device array
+ * inside the library, written with copies and a memset on stream; the call
+ * makes no cudaMalloc/cudaFree.  Each GPU that loads the library holds that
+ * array until the process exits.
+ * Limit: 256 + table bytes + (phases - 1) * nchan * in_pitch * element size
+ * must fit in 64 MiB (phases: 4 for uint8, 2 for FP16, 1 for FP32), i.e. about
+ * 21 MB of uint8 input; a larger input returns DD_ERR_INVALID (use
+ * dd_execute).  The first call on a device looks up the array's device
+ * address; make that call before any stream capture.  All calls share the
+ * array and a call overwrites what the last one left: calls whose GPU work
+ * overlaps (other streams or threads) race and must be serialized by the
+ * caller.  The table copies come from pageable host memory, so the call may
+ * wait for earlier work on stream.  Kernel-side check failures are recorded
+ * in the array only (dd_sync reports those of dd_execute). */
+dd_status dd_execute_noalloc(dd_plan_t plan, const void *in, dd_dtype dtype, int64_t in_pitch,
+                             int64_t nsamp_in, float *out, int64_t out_pitch,
+                             int64_t nsamp_out, void *stream);
+
 /* Synchronize stream and report the plan's device status word (DD_OK,
  * DD_ERR_TIMEOUT or DD_ERR_DEVICE), then clear it. */
 dd_status dd_sync(dd_plan_t plan, void *stream);

@@ -26,7 +26,7 @@ EXPORTS = [
     "dd_plan", "dd_plan_destroy", "dd_plan_maxshift", "dd_plan_nchan", "dd_plan_ndm",
     "dd_plan_dmshift", "dd_plan_get_tiles", "dd_plan_set_tiles", "dd_execute",
     "dd_execute_host", "dd_sync", "dd_profile_events", "dd_launch_count", "dd_last_error",
-    "dd_autotune",
+    "dd_autotune", "dd_execute_noalloc",
 ]
 
 
@@ -68,6 +68,7 @@ def _load() -> ctypes.CDLL:
         "dd_plan_set_tiles": (i32, [p, i32, ctypes.POINTER(Tiles)]),
         "dd_execute": (i32, [p, p, i32, i64, i64, p, i64, i64, p]),
         "dd_execute_host": (i32, [p, p, i32, i64, i64, p, i64, i64]),
+        "dd_execute_noalloc": (i32, [p, p, i32, i64, i64, p, i64, i64, p]),
         "dd_sync": (i32, [p, p]),
         "dd_profile_events": (None, [p, p]),
         "dd_autotune": (i32, [p, p, i32, i64, i64, p, i64, i64, p, i32,
@@ -197,6 +198,14 @@ class Plan:
         s = torch.cuda.current_stream(inp.device) if stream is None else stream
         self.execute_ptr(inp.data_ptr(), dtype_code(inp.dtype), inp.stride(0), nsamp_in,
                          out.data_ptr(), out.stride(0), nsamp_out, s.cuda_stream)
+
+    def execute_noalloc_ptr(self, in_ptr: int, dtype: int, in_pitch: int, nsamp_in: int,
+                            out_ptr: int, out_pitch: int, nsamp_out: int, stream: int = 0):
+        """dd_execute_noalloc on raw device pointers: for callers that cannot
+        allocate device memory; uses the library's fixed 64 MiB device array."""
+        check(lib.dd_execute_noalloc(self.handle, ctypes.c_void_p(in_ptr), dtype, in_pitch,
+                                     nsamp_in, ctypes.c_void_p(out_ptr), out_pitch, nsamp_out,
+                                     ctypes.c_void_p(stream)))
 
     def execute_host(self, inp: np.ndarray, out: np.ndarray, nsamp_in: int | None = None,
                      nsamp_out: int | None = None):

@@ -1,0 +1,138 @@
+// dd_execute_noalloc: the single-beam de-dispersion with no device
+// allocation at all.
+//
+// Some callers cannot call cudaMalloc: code running inside a custom
+// allocator or a memory-pool callback, real-time threads that must not take
+// the driver's allocation locks, and hosts that forbid the library from
+// owning device memory.  For them this entry point keeps everything the
+// kernels need beyond the caller's input and output -- the plan's device
+// tables, the status word and the byte-phase planes -- in one file-scope
+// device array of fixed size, and writes it with plain copies and a memset on
+// the caller's stream.
+//
+// The array is shared by every call in the process: a call overwrites what
+// the previous one left there, so calls whose GPU work overlaps (on
+// different streams, or from different threads) race and must be serialized
+// by the caller.  Each GPU that loads this library holds the array until the
+// process exits.
+#include <cuda_runtime.h>
+
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "dd_internal.h"
+
+namespace {
+
+constexpr size_t kNoAllocBytes = (size_t)64 << 20;  // 64 MiB
+
+// Device-side scratch of dd_execute_noalloc.  In host code this name is a
+// host-side stand-in, not a device address: the address handed to kernels
+// comes from cudaGetSymbolAddress (noalloc_base below).
+static __device__ __align__(256) uint8_t g_noalloc_scratch[kNoAllocBytes];
+
+std::mutex g_noalloc_mu;
+void *g_noalloc_ptr[64] = {nullptr};
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// Device address of the array on the current device, looked up once per
+// device (the first call on a device; it must come before any stream capture).
+dd_status noalloc_base(void **out) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64)
+        return dd::fail(DD_ERR_CUDA, "cudaGetDevice failed");
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (g_noalloc_ptr[dev] == nullptr) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || p == nullptr)
+            return dd::fail(DD_ERR_CUDA, std::string("cudaGetSymbolAddress of the fixed scratch "
+                                                     "failed: ") + cudaGetErrorString(e));
+        g_noalloc_ptr[dev] = p;
+    }
+    *out = g_noalloc_ptr[dev];
+    return DD_OK;
+}
+
+}  // namespace
+
+extern "C" dd_status dd_execute_noalloc(dd_plan_t p, const void *in, dd_dtype dtype,
+                                        int64_t in_pitch, int64_t nsamp_in, float *out,
+                                        int64_t out_pitch, int64_t nsamp_out, void *stream) {
+    using dd::fail;
+    if (!p)
+        return fail(DD_ERR_INVALID, "plan is NULL");
+    if (dtype != DD_U8 && dtype != DD_F16 && dtype != DD_F32)
+        return fail(DD_ERR_INVALID, "unknown dtype");
+    if (nsamp_out < 0 || nsamp_in < 0)
+        return fail(DD_ERR_INVALID, "negative sample count");
+    if (nsamp_out > 0 && nsamp_in < nsamp_out + p->maxshift)
+        return fail(DD_ERR_INVALID, "nsamp_in must be >= nsamp_out + maxshift");
+    if (in_pitch < nsamp_in || out_pitch < nsamp_out)
+        return fail(DD_ERR_INVALID, "pitch shorter than a row");
+    const int64_t elem = dd::elem_size(dtype);
+    if ((in_pitch * elem) % 16 != 0 || out_pitch % 4 != 0)
+        return fail(DD_ERR_INVALID, "row pitches must be multiples of 16 bytes");
+    if (nsamp_out == 0)
+        return DD_OK;
+    if (!in || !out || ((uintptr_t)in & 15u) || ((uintptr_t)out & 15u))
+        return fail(DD_ERR_INVALID, "in and out must be non-NULL and 16-byte aligned");
+
+    // Layout of the fixed array for this call.
+    const int ndm_pad = (p->ndm + 63) / 64 * 64 + 64;
+    const size_t off_status = 0;
+    const size_t off_dmshift = 256;
+    const size_t off_dm = off_dmshift + align256(sizeof(float) * (size_t)p->nchan);
+    const size_t off_perm = off_dm + align256(sizeof(float) * (size_t)ndm_pad);
+    const size_t off_planes = off_perm + align256(sizeof(int) * (size_t)ndm_pad);
+    const size_t planes = (size_t)dd::scratch_bytes(dtype, p->nchan, in_pitch * elem);
+    const size_t need = off_planes + planes;
+    if (need > kNoAllocBytes)
+        return fail(DD_ERR_INVALID,
+                    "input too large for dd_execute_noalloc: it needs " + std::to_string(need) +
+                        " bytes of its fixed " + std::to_string(kNoAllocBytes) +
+                        "-byte scratch; use dd_execute");
+
+    dd::Geometry g;
+    dd_status st = dd::plan_geometry(p, dtype, &g);
+    if (st != DD_OK)
+        return st;
+    void *base = nullptr;
+    if ((st = noalloc_base(&base)) != DD_OK)
+        return st;
+    uint8_t *b = static_cast<uint8_t *>(base);
+
+    // Plan tables as the kernels expect them: DMs ascending, padded with the
+    // largest; perm maps a sorted position to the caller's row (-1: padding).
+    std::vector<float> dms(ndm_pad, p->dm_sorted.back());
+    std::vector<int> perm(ndm_pad, -1);
+    for (int k = 0; k < p->ndm; ++k) {
+        dms[k] = p->dm_sorted[k];
+        perm[k] = p->order[k];
+    }
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaMemsetAsync(b + off_status, 0, sizeof(int), s);  // status starts clear
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(b + off_dmshift, p->dmshift.data(), sizeof(float) * p->nchan,
+                            cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(b + off_dm, dms.data(), sizeof(float) * ndm_pad,
+                            cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(b + off_perm, perm.data(), sizeof(int) * ndm_pad,
+                            cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess)
+        return fail(DD_ERR_CUDA, std::string("table copy: ") + cudaGetErrorString(e));
+
+    dd::DevTables dt;
+    dt.dmshift = reinterpret_cast<float *>(b + off_dmshift);
+    dt.dm_sorted = reinterpret_cast<float *>(b + off_dm);
+    dt.perm = reinterpret_cast<int *>(b + off_perm);
+    dt.status = reinterpret_cast<int *>(b + off_status);
+    dt.ndm_pad = ndm_pad;
+    return dd::launch_dedisperse(p, g, dt, in, dtype, in_pitch, nsamp_in, out, out_pitch,
+                                 nsamp_out, planes ? b + off_planes : nullptr, stream);
+}
