@@ -26,6 +26,7 @@ constexpr int kFloatBlock = 64;
 
 constexpr int kMaxSmem = 232448;  // 227 KB dynamic shared memory per CTA
 constexpr int kMaxDmPerCta = 64;   // DMs per CTA (offset-table columns, DM padding)
+constexpr int kStageMeta = 32;     // bytes of a stage record in shared memory
 // Consumer warps per CTA (plus one producer warp), from the registers a
 // thread needs: accumulators 2*DT*NW (uint8) + two load buffers 4*NW + ~24.
 // 13 warps leave 128 registers a thread (at most 4 warps per SM
@@ -66,6 +67,7 @@ struct Geometry {
     int t_cta = 0;        // samples per CTA
     int ntile_d = 0;      // DM tiles
     int wp = 0;           // bytes of one phase row in shared memory
+    int stage_bytes = 0;  // bytes of one ring stage (chan_per_stage rows, every phase)
     int nstages = 0;      // shared-memory stages in the copy ring
     int zero_bytes = 0;   // zero row read by padding channels
     int smem = 0;         // dynamic shared memory per CTA

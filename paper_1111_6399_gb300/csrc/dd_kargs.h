@@ -8,7 +8,8 @@
 
 namespace dd {
 
-struct KArgs {
+// One beam: its buffers, plan tables and launch geometry.
+struct BeamArgs {
     const uint8_t *in;
     const uint8_t *planes;  // byte-phase planes 1..NPH-1 (NULL for FP32)
     int64_t plane_stride;   // bytes between planes
@@ -17,16 +18,29 @@ struct KArgs {
     float *out;
     int64_t out_pitch;      // floats between DM rows
     int64_t nsamp_out;
-    const float *dmshift;
-    const float *dm_sorted;
-    const int *perm;
+    const float *dmshift;   // [nchan]
+    const float *dm_sorted; // [ndm padded by >= 64]
+    const int *perm;        // sorted DM -> output row, -1 for padding
+    int64_t tile_begin;     // first global tile of this beam
     int nchan;
+    int ntile_d;            // DM tiles of this beam
+    int wp;                 // bytes per phase row in shared memory
+    int pad;
+};
+
+// One launch: a single beam (beam0, beams == NULL, one tile per CTA) or a
+// batch (beams[], tiles claimed dynamically through tile_counter).
+struct KArgs {
+    BeamArgs beam0;
+    const BeamArgs *beams;
+    int nbeams;
+    int64_t total_tiles;
+    int *tile_counter;      // zeroed before the launch; NULL: tile = blockIdx.x
     int dm_warps;
     int time_warps;
-    int ntile_d;
-    int cstage;
-    int nstages;
-    int wp;                 // bytes per phase row
+    int cstage;             // channels per ring stage
+    int nstages;            // stages in the ring
+    int stage_bytes;        // capacity of one ring stage
     int zero_bytes;         // bytes of the zero row (padding channels)
     uint32_t one;           // the constant 1, opaque to the compiler
     int *status;
@@ -44,5 +58,8 @@ cudaError_t launch_planes_u8(const uint8_t *in, int64_t pitch_b, int nchan, int6
                              uint8_t *planes, int64_t plane_stride, cudaStream_t s);
 cudaError_t launch_planes_f16(const uint8_t *in, int64_t pitch_b, int nchan, int64_t nsamp_in,
                               uint8_t *planes, int64_t plane_stride, cudaStream_t s);
+
+// Shared-memory bytes of the per-stage metadata record.
+constexpr int kStageMetaBytes = 32;
 
 }  // namespace dd

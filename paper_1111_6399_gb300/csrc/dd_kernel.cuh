@@ -1,4 +1,3 @@
-#pragma once
 // Brute-force incoherent de-dispersion kernels for sm_103a (GB300).
 //
 //   out[d][t] = sum_c in[c][t + s(c,d)],   s(c,d) = trunc(dm[d] * dmshift[c])
@@ -8,9 +7,10 @@
 // shift.  Their sm_103a form here:
 //
 //  * Accumulators in registers.  A consumer thread owns dm_per_thread trial
-//    DMs x 8 four-byte words of output time (32 uint8 samples), lane-interleaved
-//    so each shared-memory read of a warp covers 32 consecutive banks.  A CTA
-//    owns a rectangle of (DM,t) (Fig. 2).
+//    DMs x 4 or 8 four-byte words of output time (16 or 32 uint8 samples),
+//    lane-interleaved so each shared-memory read of a warp covers 32
+//    consecutive banks.  A tile -- one CTA's work item -- is a rectangle of
+//    (DM,t) (Fig. 2).
 //  * Data next to the SMs.  A producer warp stages each channel's window
 //    [t0 + s(c,dm_min), t0 + T + s(c,dm_max)) with TMA bulk copies (no
 //    multicast) into a ring of shared-memory stages handed over through
@@ -20,8 +20,10 @@
 //    is staged once per byte phase (1..3 or 2 bytes later), fetched from phase
 //    planes that a pre-pass writes to global scratch; every shifted read is
 //    then an aligned, conflict-free LDS.32.
-//  * Shift arithmetic.  One FP32 multiply and one truncation per (channel,
-//    DM) per thread, reused for 8 words.
+//  * Shift arithmetic.  The producer computes, per staged channel and DM of
+//    the tile, the shared-memory offset of the shifted window (one FP32
+//    multiply and one truncation) into a small table; consumers fetch the
+//    offsets of a channel pair with one LDS.64.
 //  * uint8 sums use 16-bit SWAR lanes: for a word x of 4 samples, L1 += x and
 //    L2 += (x >> 8) & 0x00ff00ff.  After at most 256 channels
 //    L2 = {sum b1, sum b3} and L1 - 256*L2 = {sum b0, sum b2} exactly; these are
@@ -31,9 +33,18 @@
 //  * FP16/FP32 sums: FP32 partials over blocks of 64 channels, combined into a
 //    running sum with TwoSum compensation (error ~1e-7 of sum |in|).
 //
+// Work distribution.  The producer decides which tile the CTA works on and
+// tags every stage with it (beam, DM tile, first sample, stage number); the
+// consumers follow that stream until a terminating stage.  A single-beam
+// launch gives each CTA one tile (blockIdx.x); a batch launch is persistent
+// (one CTA per SM) and the producer claims tiles of many beams, largest
+// first, from an atomic counter.
+//
 // Every mbarrier wait is bounded by the global timer; a wait that runs out
 // records a timeout in the status word and the thread leaves (the producer
 // first waits, again bounded, for the copies it issued).
+#pragma once
+
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -47,7 +58,15 @@ namespace {
 
 constexpr uint64_t kWaitLimitNs = 2000000000ull;  // 2 s
 
-
+// Stage record written by the producer before it releases a stage.
+struct __align__(16) StageMeta {
+    int beam;     // -1: no more tiles
+    int td;       // DM tile
+    int st;       // stage number within the tile
+    int nstage;   // stages of the tile
+    int64_t t0;   // first output sample of the tile
+    int64_t pad;
+};
 
 __device__ __forceinline__ uint32_t smem_addr(const void *p) {
     return (uint32_t)__cvta_generic_to_shared(p);
@@ -207,23 +226,36 @@ __global__ void __launch_bounds__(256) phase_planes_kernel(const uint8_t *__rest
     }
 }
 
+__device__ __forceinline__ const BeamArgs &beam_at(const KArgs &a, int i) {
+    return a.beams ? a.beams[i] : a.beam0;
+}
+
+// Beam owning global tile `tile` (beams are laid out by increasing tile_begin).
+__device__ __forceinline__ int beam_of_tile(const KArgs &a, int64_t tile) {
+    if (a.beams == nullptr)
+        return 0;
+    int lo = 0, hi = a.nbeams - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (a.beams[mid].tile_begin <= tile)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    return lo;
+}
+
 // ---------------------------------------------------------------------------
 // The de-dispersion kernel.  ELEM = bytes per sample (1, 2, 4); DT = DMs per
-// consumer thread; NW = 4-byte words per DM per consumer thread (4 or 8).  Warps 0..ncw-1 consume, warp ncw produces.
-//
-// Per stage the producer also writes, for every staged channel row r and
-// every DM k of the CTA, the shared-memory byte offset of that DM's shifted
-// window (row base + ELEM*s(c,k) + phase row), so a consumer fetches its DMs'
-// offsets with one vector LDS instead of recomputing the shift.  Consumers
-// software-pipeline: the 16 words of the next (channel pair, DM) are loaded
-// into the alternate register buffer before the current ones are summed.
+// consumer thread; NW = 4-byte words per DM per consumer thread (4 or 8).
+// Warps 0..ncw-1 consume, warp ncw produces.
 // ---------------------------------------------------------------------------
 template <int ELEM, int DT, int NW>
 __global__ void __launch_bounds__(32 * (max_consumer_warps(DT, NW) + 1), 1)
-    dedisperse_kernel(const KArgs a) {
+    dedisperse_kernel(const __grid_constant__ KArgs a) {
     constexpr int NPH = 4 / ELEM;            // phase copies per row
     constexpr int SPW = 4 / ELEM;            // samples per 4-byte word
-    constexpr int SPAN = 32 * NW * SPW;  // samples per warp
+    constexpr int SPAN = 32 * NW * SPW;      // samples per warp
     constexpr int FLUSH = (ELEM == 1) ? kSwarChannels : kFloatBlock;
 
     extern __shared__ __align__(128) uint8_t smem[];
@@ -233,24 +265,19 @@ __global__ void __launch_bounds__(32 * (max_consumer_warps(DT, NW) + 1), 1)
     const int ncw = a.dm_warps * a.time_warps;  // consumer warps
     const int dm_cta = DT * a.dm_warps;
     const int t_cta = SPAN * a.time_warps;
-    const int td = blockIdx.x % a.ntile_d;
-    const int64_t t0 = (int64_t)(blockIdx.x / a.ntile_d) * t_cta;
 
     const int cstage = a.cstage;
     const int nst = a.nstages;
-    const int wp = a.wp;
-    const int row_bytes = NPH * wp;
-    const int stage_bytes = cstage * row_bytes;
+    const int stage_bytes = a.stage_bytes;
     const int tab_stride = cstage * dm_cta;  // ints per stage in the offset table
     int *atab = reinterpret_cast<int *>(smem + nst * stage_bytes);
-    uint8_t *zero = smem + nst * stage_bytes + ((nst * tab_stride * 4 + 15) & ~15);
+    StageMeta *meta = reinterpret_cast<StageMeta *>(
+        smem + nst * stage_bytes + ((nst * tab_stride * 4 + 15) & ~15));
+    uint8_t *zero = reinterpret_cast<uint8_t *>(meta) + nst * kStageMetaBytes;
     uint64_t *mbar = reinterpret_cast<uint64_t *>(zero + a.zero_bytes);
     const uint32_t full0 = smem_addr(&mbar[0]);
     const uint32_t empty0 = smem_addr(&mbar[nst]);
     const int zero_off = (int)(zero - smem);
-
-    const int kcta = td * dm_cta;
-    const int nstage = (a.nchan + cstage - 1) / cstage;
 
     for (int i = tid; i < a.zero_bytes / 16; i += blockDim.x)
         reinterpret_cast<uint4 *>(zero)[i] = make_uint4(0, 0, 0, 0);
@@ -265,116 +292,172 @@ __global__ void __launch_bounds__(32 * (max_consumer_warps(DT, NW) + 1), 1)
 
     if (warp == ncw) {
         // ------------------------------ producer ------------------------------
-        const float dm_min = a.dm_sorted[kcta];
-        const float dm_max = a.dm_sorted[kcta + dm_cta - 1];
-        float dmk[2];  // DM columns lane and lane + 32 (dm_cta <= 64, host-checked)
-        dmk[0] = a.dm_sorted[kcta + min(lane, dm_cta - 1)];
-        dmk[1] = a.dm_sorted[kcta + min(lane + 32, dm_cta - 1)];
-        int issued = 0;
+        int64_t g = 0;  // ring position of the next stage
         bool ok = true;
-        // dmshift of the rows of the next stage (lane r: rows r and r + 32),
-        // loaded one stage ahead so the load latency overlaps the empty wait.
-        float ds_next[2];
-        for (int h = 0; h < 2; ++h) {
-            const int c = lane + 32 * h;
-            ds_next[h] = (lane + 32 * h < cstage && c < a.nchan) ? a.dmshift[c] : 0.0f;
-        }
-        for (int st = 0; st < nstage; ++st) {
-            const int b = st % nst;
-            const int n = st / nst;
-            const float ds_cur[2] = {ds_next[0], ds_next[1]};
-            for (int h = 0; h < 2; ++h) {
-                const int c = (st + 1) * cstage + lane + 32 * h;
-                ds_next[h] = (st + 1 < nstage && lane + 32 * h < cstage && c < a.nchan)
-                                 ? a.dmshift[c] : 0.0f;
+        bool first = true;
+        for (;;) {
+            int64_t tile;
+            if (a.tile_counter) {
+                int t = 0;
+                if (lane == 0)
+                    t = atomicAdd(a.tile_counter, 1);
+                tile = __shfl_sync(0xffffffffu, t, 0);
+            } else {
+                tile = first ? (int64_t)blockIdx.x : a.total_tiles;
             }
-            if (n > 0 && !mbar_wait(empty0 + 8 * b, (n - 1) & 1)) {
-                ok = false;
+            first = false;
+            if (tile >= a.total_tiles)
                 break;
-            }
-            uint8_t *buf = smem + b * stage_bytes;
-            int *tab = atab + b * tab_stride;
-            uint32_t my_bytes[2] = {0u, 0u};
-            int64_t my_first[2] = {0, 0};
-            int my_base[2] = {zero_off, zero_off};
-            float my_ds[2] = {0.0f, 0.0f};
-            bool bad = false;
-            // Window of each staged row (lane r holds rows r and r + 32).
+            const int bi = beam_of_tile(a, tile);
+            const BeamArgs &B = beam_at(a, bi);
+            const int64_t local = tile - B.tile_begin;
+            const int td = (int)(local % B.ntile_d);
+            const int64_t t0 = (local / B.ntile_d) * t_cta;
+            const int kcta = td * dm_cta;
+            const int wp = B.wp;
+            const int row_bytes = NPH * wp;
+            const int nstage = (B.nchan + cstage - 1) / cstage;
+            const float dm_min = B.dm_sorted[kcta];
+            const float dm_max = B.dm_sorted[kcta + dm_cta - 1];
+            float dmk[2];  // DM columns lane and lane + 32 (dm_cta <= 64, host-checked)
+            dmk[0] = B.dm_sorted[kcta + min(lane, dm_cta - 1)];
+            dmk[1] = B.dm_sorted[kcta + min(lane + 32, dm_cta - 1)];
+            // dmshift of the rows of the next stage (lane r: rows r and r + 32),
+            // loaded one stage ahead so the load latency overlaps the empty wait.
+            float ds_next[2];
             for (int h = 0; h < 2; ++h) {
-                const int r = lane + 32 * h;
-                const int c = st * cstage + r;
-                if (r >= cstage || c >= a.nchan)
-                    continue;
-                const float ds = ds_cur[h];
-                const int64_t smin = shift_of(dm_min, ds);
-                const int64_t smax = shift_of(dm_max, ds);
-                const int64_t first = (t0 + smin) & ~(int64_t)(16 / ELEM - 1);
-                int64_t end = t0 + t_cta + smax;
-                if (end > a.nsamp_in)
-                    end = a.nsamp_in;
-                const int64_t bytes = ((end - first) * ELEM + 15) & ~(int64_t)15;
-                if (bytes > wp - 16 || bytes <= 0) {  // excluded by the host checks
-                    bad = true;
-                    continue;
-                }
-                my_base[h] = (int)(buf + r * row_bytes - smem) + (int)(ELEM * (t0 - first));
-                my_ds[h] = ds;
-                my_bytes[h] = (uint32_t)bytes;
-                my_first[h] = first;
+                const int c = lane + 32 * h;
+                ds_next[h] = (lane + 32 * h < cstage && c < B.nchan) ? B.dmshift[c] : 0.0f;
             }
-            if (bad)
-                record(a.status, kDevCheck);
-            // Copies first: the expected byte count is registered without an
-            // arrival, the copies are issued, and the offset table is written
-            // while they are in flight; the arrival then releases the stage
-            // (the phase completes once it and every byte are in).
-            uint32_t total = (my_bytes[0] + my_bytes[1]) * NPH;
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1)
-                total += __shfl_xor_sync(0xffffffffu, total, o);
-            if (lane == 0)
-                mbar_expect_tx(full0 + 8 * b, total);
-            __syncwarp();
-            for (int h = 0; h < 2; ++h) {
-                const int r = lane + 32 * h;
-                if (r >= cstage || my_bytes[h] == 0)
-                    continue;
-                const int c = st * cstage + r;
-                const int64_t off = (int64_t)c * a.in_pitch_b + my_first[h] * ELEM;
-                const uint32_t dst = smem_addr(buf + r * row_bytes);
-                bulk_g2s(dst, a.in + off, my_bytes[h], full0 + 8 * b);
-#pragma unroll
-                for (int p = 1; p < NPH; ++p)
-                    bulk_g2s(dst + p * wp, a.planes + (p - 1) * a.plane_stride + off, my_bytes[h],
-                             full0 + 8 * b);
-            }
-            // Offset table: row r, DM k -> smem offset of the shifted window.
-            for (int r = 0; r < cstage; ++r) {
-                const int base = __shfl_sync(0xffffffffu, my_base[r >> 5], r & 31);
-                const float ds = __shfl_sync(0xffffffffu, my_ds[r >> 5], r & 31);
-#pragma unroll
+            for (int st = 0; st < nstage; ++st, ++g) {
+                const int b = (int)(g % nst);
+                const int64_t n = g / nst;
+                const float ds_cur[2] = {ds_next[0], ds_next[1]};
                 for (int h = 0; h < 2; ++h) {
-                    const int k = lane + 32 * h;
-                    if (k < dm_cta) {
-                        const int s = shift_of(dmk[h], ds);
-                        // pair layout: [r/2][k][r%2], so one LDS.64 gives both rows
-                        tab[((r >> 1) * dm_cta + k) * 2 + (r & 1)] =
-                            base + ELEM * s + (s & (NPH - 1)) * (wp - ELEM);
+                    const int c = (st + 1) * cstage + lane + 32 * h;
+                    ds_next[h] = (st + 1 < nstage && lane + 32 * h < cstage && c < B.nchan)
+                                     ? B.dmshift[c] : 0.0f;
+                }
+                if (n > 0 && !mbar_wait(empty0 + 8 * b, (uint32_t)((n - 1) & 1))) {
+                    ok = false;
+                    break;
+                }
+                uint8_t *buf = smem + b * stage_bytes;
+                int *tab = atab + b * tab_stride;
+                uint32_t my_bytes[2] = {0u, 0u};
+                int64_t my_first[2] = {0, 0};
+                int my_base[2] = {zero_off, zero_off};
+                float my_ds[2] = {0.0f, 0.0f};
+                bool bad = false;
+                // Window of each staged row (lane r holds rows r and r + 32).
+                for (int h = 0; h < 2; ++h) {
+                    const int r = lane + 32 * h;
+                    const int c = st * cstage + r;
+                    if (r >= cstage || c >= B.nchan)
+                        continue;
+                    const float ds = ds_cur[h];
+                    const int64_t smin = shift_of(dm_min, ds);
+                    const int64_t smax = shift_of(dm_max, ds);
+                    const int64_t firsts = (t0 + smin) & ~(int64_t)(16 / ELEM - 1);
+                    int64_t end = t0 + t_cta + smax;
+                    if (end > B.nsamp_in)
+                        end = B.nsamp_in;
+                    const int64_t bytes = ((end - firsts) * ELEM + 15) & ~(int64_t)15;
+                    if (bytes > wp - 16 || bytes <= 0 || cstage * row_bytes > stage_bytes) {
+                        bad = true;  // excluded by the host checks
+                        continue;
+                    }
+                    my_base[h] = (int)(buf + r * row_bytes - smem) + (int)(ELEM * (t0 - firsts));
+                    my_ds[h] = ds;
+                    my_bytes[h] = (uint32_t)bytes;
+                    my_first[h] = firsts;
+                }
+                if (bad)
+                    record(a.status, kDevCheck);
+                if (lane == 0) {
+                    StageMeta m;
+                    m.beam = bi;
+                    m.td = td;
+                    m.st = st;
+                    m.nstage = nstage;
+                    m.t0 = t0;
+                    m.pad = 0;
+                    meta[b] = m;
+                }
+                // Copies first: the expected byte count is registered without an
+                // arrival, the copies are issued, and the offset table is written
+                // while they are in flight; the arrival then releases the stage
+                // (the phase completes once it and every byte are in).
+                uint32_t total = (my_bytes[0] + my_bytes[1]) * NPH;
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1)
+                    total += __shfl_xor_sync(0xffffffffu, total, o);
+                if (lane == 0)
+                    mbar_expect_tx(full0 + 8 * b, total);
+                __syncwarp();
+                for (int h = 0; h < 2; ++h) {
+                    const int r = lane + 32 * h;
+                    if (r >= cstage || my_bytes[h] == 0)
+                        continue;
+                    const int c = st * cstage + r;
+                    const int64_t off = (int64_t)c * B.in_pitch_b + my_first[h] * ELEM;
+                    const uint32_t dst = smem_addr(buf + r * row_bytes);
+                    bulk_g2s(dst, B.in + off, my_bytes[h], full0 + 8 * b);
+#pragma unroll
+                    for (int p = 1; p < NPH; ++p)
+                        bulk_g2s(dst + p * wp, B.planes + (p - 1) * B.plane_stride + off,
+                                 my_bytes[h], full0 + 8 * b);
+                }
+                // Offset table: row r, DM k -> smem offset of the shifted window.
+                for (int r = 0; r < cstage; ++r) {
+                    const int base = __shfl_sync(0xffffffffu, my_base[r >> 5], r & 31);
+                    const float ds = __shfl_sync(0xffffffffu, my_ds[r >> 5], r & 31);
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        const int k = lane + 32 * h;
+                        if (k < dm_cta) {
+                            const int s = shift_of(dmk[h], ds);
+                            // pair layout [r/2][k][r%2]: one LDS.64 gives both rows
+                            tab[((r >> 1) * dm_cta + k) * 2 + (r & 1)] =
+                                base + ELEM * s + (s & (NPH - 1)) * (wp - ELEM);
+                        }
                     }
                 }
+                __syncwarp();
+                if (lane == 0)
+                    mbar_arrive(full0 + 8 * b);
             }
-            __syncwarp();
-            if (lane == 0)
-                mbar_arrive(full0 + 8 * b);
-            issued = st + 1;
+            if (!ok)
+                break;
+        }
+        const int64_t real = g;  // stages handed to the consumers
+        if (ok) {
+            // Terminating stage: tells the consumers there is no further tile.
+            const int b = (int)(g % nst);
+            const int64_t n = g / nst;
+            if (n > 0 && !mbar_wait(empty0 + 8 * b, (uint32_t)((n - 1) & 1))) {
+                ok = false;
+            } else {
+                if (lane == 0) {
+                    StageMeta m;
+                    m.beam = -1;
+                    m.td = m.st = m.nstage = 0;
+                    m.t0 = 0;
+                    m.pad = 0;
+                    meta[b] = m;
+                }
+                __syncwarp();
+                if (lane == 0)
+                    mbar_arrive(full0 + 8 * b);
+            }
         }
         if (!ok)
             record(a.status, kDevTimeout);
-        // Leave only once the last stages issued have landed (and, normally,
-        // been released by the consumers); bounded.
-        for (int st = (issued > nst ? issued - nst : 0); st < issued; ++st) {
-            const int b = st % nst;
-            if (!mbar_wait(ok ? empty0 + 8 * b : full0 + 8 * b, (st / nst) & 1)) {
+        // Leave only once the last stages handed over have landed (and,
+        // normally, been released by the consumers); bounded.
+        for (int64_t q = (real > nst ? real - nst : 0); q < real; ++q) {
+            const int b = (int)(q % nst);
+            if (!mbar_wait(ok ? empty0 + 8 * b : full0 + 8 * b, (uint32_t)((q / nst) & 1))) {
                 record(a.status, kDevTimeout);
                 break;
             }
@@ -385,13 +468,12 @@ __global__ void __launch_bounds__(32 * (max_consumer_warps(DT, NW) + 1), 1)
     // ------------------------------- consumers --------------------------------
     const int wdi = warp % a.dm_warps;
     const int wti = warp / a.dm_warps;
-    const int kthr = kcta + wdi * DT;
     const int kw = wdi * DT;  // this thread's first DM column in the offset table
     const int thr_off = ELEM * (wti * SPAN) + 4 * lane;
     const uint32_t one = a.one;
 
     uint32_t L1[DT][NW], L2[DT][NW];                            // uint8 SWAR
-    float P[DT][NW][SPW], S[DT][NW][SPW], C[DT][NW][SPW];  // floats
+    float P[DT][NW][SPW], S[DT][NW][SPW], C[DT][NW][SPW];      // floats
 #pragma unroll
     for (int j = 0; j < DT; ++j)
 #pragma unroll
@@ -406,15 +488,18 @@ __global__ void __launch_bounds__(32 * (max_consumer_warps(DT, NW) + 1), 1)
             }
         }
 
+    // Current tile (from the stage records).
+    int beam = 0, kthr = 0;
+    int64_t tw = 0;
     int since_flush = 0;
     bool flushed_once = false;
-    const int64_t tw = t0 + (int64_t)wti * SPAN;
 
     auto flush_u8 = [&]() {
+        const BeamArgs &B = beam_at(a, beam);
 #pragma unroll
         for (int j = 0; j < DT; ++j) {
-            const int row = a.perm[kthr + j];
-            float *orow = a.out + (int64_t)row * a.out_pitch;
+            const int row = B.perm[kthr + j];
+            float *orow = B.out + (int64_t)row * B.out_pitch;
 #pragma unroll
             for (int k = 0; k < NW; ++k) {
                 const uint32_t lo = L1[j][k] - (L2[j][k] << 8);
@@ -429,8 +514,8 @@ __global__ void __launch_bounds__(32 * (max_consumer_warps(DT, NW) + 1), 1)
                 L2[j][k] = 0u;
                 if (row >= 0) {
                     const int64_t t = tw + 4 * (lane + 32 * k);
-                    if (t < a.nsamp_out)
-                        store4(orow, t, a.nsamp_out, v, flushed_once);
+                    if (t < B.nsamp_out)
+                        store4(orow, t, B.nsamp_out, v, flushed_once);
                 }
             }
         }
@@ -454,6 +539,38 @@ __global__ void __launch_bounds__(32 * (max_consumer_warps(DT, NW) + 1), 1)
                     S[j][k][e] = s;
                     P[j][k][e] = 0.f;
                 }
+    };
+
+    auto store_float = [&]() {
+        const BeamArgs &B = beam_at(a, beam);
+#pragma unroll
+        for (int j = 0; j < DT; ++j) {
+            const int row = B.perm[kthr + j];
+            float *orow = B.out + (int64_t)row * B.out_pitch;
+#pragma unroll
+            for (int k = 0; k < NW; ++k) {
+                const int64_t t = tw + SPW * (lane + 32 * k);
+                if (row >= 0) {
+                    if (SPW == 1) {
+                        if (t < B.nsamp_out)
+                            orow[t] = __fadd_rn(S[j][k][0], C[j][k][0]);
+                    } else {
+                        if (t + 1 < B.nsamp_out) {
+                            *reinterpret_cast<float2 *>(orow + t) =
+                                make_float2(__fadd_rn(S[j][k][0], C[j][k][0]),
+                                            __fadd_rn(S[j][k][SPW - 1], C[j][k][SPW - 1]));
+                        } else if (t < B.nsamp_out) {
+                            orow[t] = __fadd_rn(S[j][k][0], C[j][k][0]);
+                        }
+                    }
+                }
+#pragma unroll
+                for (int e = 0; e < SPW; ++e) {
+                    S[j][k][e] = 0.f;
+                    C[j][k][e] = 0.f;
+                }
+            }
+        }
     };
 
     auto load_words = [&](int2 off, uint32_t (&x)[NW], uint32_t (&y)[NW]) {
@@ -486,27 +603,37 @@ __global__ void __launch_bounds__(32 * (max_consumer_warps(DT, NW) + 1), 1)
         }
     };
 
-    // Iterations (channel pair q, DM j) run in order; the words of the next
-    // iteration are loaded into the other register buffer before the current
-    // ones are summed.  The pair loop is unrolled by two, so the buffers
-    // alternate with the (compile-time) parity of the iteration.
+    // Stages run in ring order; within a stage the iterations (channel pair q,
+    // DM j) run in order and the words of the next iteration are loaded into
+    // the other register buffer before the current ones are summed.  The pair
+    // loop is unrolled by two, so the buffers alternate with the
+    // (compile-time) parity of the iteration.
     const int npairs = cstage / 2;  // even: chan_per_stage is a multiple of 4
     uint32_t xa[NW], ya[NW], xb[NW], yb[NW];
-    if (nstage > 0) {
-        if (!mbar_wait(full0, 0)) {
+    for (int64_t g = 0;; ++g) {
+        const int b = (int)(g % nst);
+        if (!mbar_wait(full0 + 8 * b, (uint32_t)((g / nst) & 1))) {
             record(a.status, kDevTimeout);
             return;
         }
-        load_words(offsets(0, 0, 0), xa, ya);
-    }
-    for (int st = 0; st < nstage; ++st) {
-        const int b = st % nst;
+        const StageMeta m = meta[b];
+        if (m.beam < 0)
+            break;  // no further tile
+        if (m.st == 0) {
+            beam = m.beam;
+            kthr = m.td * dm_cta + kw;
+            tw = m.t0 + (int64_t)wti * SPAN;
+            since_flush = 0;
+            flushed_once = false;
+            load_words(offsets(b, 0, 0), xa, ya);
+        }
         since_flush += cstage;
+        const bool last = m.st + 1 == m.nstage;
         // Widen (uint8) or close a compensated block (floats) after this stage
         // if the next one would overflow it.  The next stage's first words are
         // then loaded after the widening, so no prefetched buffer is live
         // across it.
-        const bool widen = st + 1 < nstage && since_flush + cstage > FLUSH;
+        const bool widen = !last && since_flush + cstage > FLUSH;
         for (int q = 0; q < npairs; q += 2) {
 #pragma unroll
             for (int i = 0; i < 2 * DT; ++i) {
@@ -525,9 +652,9 @@ __global__ void __launch_bounds__(32 * (max_consumer_warps(DT, NW) + 1), 1)
                     __syncwarp();
                     if (lane == 0)
                         mbar_arrive(empty0 + 8 * b);
-                    if (st + 1 < nstage && !widen) {
-                        const int bn = (st + 1) % nst;
-                        if (!mbar_wait(full0 + 8 * bn, ((st + 1) / nst) & 1)) {
+                    if (!last && !widen) {
+                        const int bn = (int)((g + 1) % nst);
+                        if (!mbar_wait(full0 + 8 * bn, (uint32_t)(((g + 1) / nst) & 1))) {
                             record(a.status, kDevTimeout);
                             return;
                         }
@@ -543,45 +670,23 @@ __global__ void __launch_bounds__(32 * (max_consumer_warps(DT, NW) + 1), 1)
             else
                 block_float();
             since_flush = 0;
-            const int bn = (st + 1) % nst;  // 2*DT iterations per pair step: next is xa/ya
-            if (!mbar_wait(full0 + 8 * bn, ((st + 1) / nst) & 1)) {
+            const int bn = (int)((g + 1) % nst);  // 2*DT iterations per pair step: next is xa/ya
+            if (!mbar_wait(full0 + 8 * bn, (uint32_t)(((g + 1) / nst) & 1))) {
                 record(a.status, kDevTimeout);
                 return;
             }
             load_words(offsets(bn, 0, 0), xa, ya);
         }
-    }
-
-    if (ELEM == 1) {
-        flush_u8();
-    } else {
-        block_float();
-#pragma unroll
-        for (int j = 0; j < DT; ++j) {
-            const int row = a.perm[kthr + j];
-            if (row < 0)
-                continue;
-            float *orow = a.out + (int64_t)row * a.out_pitch;
-#pragma unroll
-            for (int k = 0; k < NW; ++k) {
-                const int64_t t = tw + SPW * (lane + 32 * k);
-                if (SPW == 1) {
-                    if (t < a.nsamp_out)
-                        orow[t] = __fadd_rn(S[j][k][0], C[j][k][0]);
-                } else {
-                    if (t + 1 < a.nsamp_out) {
-                        *reinterpret_cast<float2 *>(orow + t) =
-                            make_float2(__fadd_rn(S[j][k][0], C[j][k][0]),
-                                        __fadd_rn(S[j][k][SPW - 1], C[j][k][SPW - 1]));
-                    } else if (t < a.nsamp_out) {
-                        orow[t] = __fadd_rn(S[j][k][0], C[j][k][0]);
-                    }
-                }
+        if (last) {
+            if (ELEM == 1) {
+                flush_u8();
+            } else {
+                block_float();
+                store_float();
             }
         }
     }
 }
-
 
 template <int ELEM, int DT, int NW>
 cudaError_t launch_one(const KArgs &a, unsigned grid, int threads, int smem, cudaStream_t s) {

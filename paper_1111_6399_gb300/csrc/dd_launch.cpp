@@ -24,25 +24,31 @@ dd_status launch_dedisperse(dd_plan_s *p, const Geometry &g, const DevTables &dt
                             int64_t out_pitch, int64_t nsamp_out, void *scratch, void *stream) {
     if (nsamp_out == 0)
         return DD_OK;
-    KArgs a;
-    a.in = static_cast<const uint8_t *>(in);
-    a.in_pitch_b = in_pitch * g.elem;
-    a.planes = static_cast<const uint8_t *>(scratch);
-    a.plane_stride = (int64_t)p->nchan * a.in_pitch_b;
-    a.nsamp_in = nsamp_in;
-    a.out = out;
-    a.out_pitch = out_pitch;
-    a.nsamp_out = nsamp_out;
-    a.dmshift = dt.dmshift;
-    a.dm_sorted = dt.dm_sorted;
-    a.perm = dt.perm;
-    a.nchan = p->nchan;
+    KArgs a{};
+    BeamArgs &b = a.beam0;
+    b.in = static_cast<const uint8_t *>(in);
+    b.in_pitch_b = in_pitch * g.elem;
+    b.planes = static_cast<const uint8_t *>(scratch);
+    b.plane_stride = (int64_t)p->nchan * b.in_pitch_b;
+    b.nsamp_in = nsamp_in;
+    b.out = out;
+    b.out_pitch = out_pitch;
+    b.nsamp_out = nsamp_out;
+    b.dmshift = dt.dmshift;
+    b.dm_sorted = dt.dm_sorted;
+    b.perm = dt.perm;
+    b.tile_begin = 0;
+    b.nchan = p->nchan;
+    b.ntile_d = g.ntile_d;
+    b.wp = g.wp;
+    a.beams = nullptr;
+    a.nbeams = 1;
+    a.tile_counter = nullptr;
     a.dm_warps = g.tiles.dm_warps;
     a.time_warps = g.tiles.time_warps;
-    a.ntile_d = g.ntile_d;
     a.cstage = g.tiles.chan_per_stage;
     a.nstages = g.nstages;
-    a.wp = g.wp;
+    a.stage_bytes = g.stage_bytes;
     a.zero_bytes = g.zero_bytes;
     a.one = 1u;
     a.status = dt.status;
@@ -50,18 +56,19 @@ dd_status launch_dedisperse(dd_plan_s *p, const Geometry &g, const DevTables &dt
     const int64_t ntiles = ntile_t * g.ntile_d;
     if (ntiles > 0x7fffffffLL)
         return fail(DD_ERR_INVALID, "too many tiles for one launch");
+    a.total_tiles = ntiles;
     if (g.nph > 1 && scratch == nullptr)
         return fail(DD_ERR_INVALID, "phase-plane scratch missing");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     cudaError_t e = cudaSuccess;
     int launches = 1;
     if (dtype == DD_U8) {
-        e = launch_planes_u8(a.in, a.in_pitch_b, p->nchan, nsamp_in, (uint8_t *)scratch,
-                             a.plane_stride, s);
+        e = launch_planes_u8(b.in, b.in_pitch_b, p->nchan, nsamp_in, (uint8_t *)scratch,
+                             b.plane_stride, s);
         ++launches;
     } else if (dtype == DD_F16) {
-        e = launch_planes_f16(a.in, a.in_pitch_b, p->nchan, nsamp_in, (uint8_t *)scratch,
-                              a.plane_stride, s);
+        e = launch_planes_f16(b.in, b.in_pitch_b, p->nchan, nsamp_in, (uint8_t *)scratch,
+                              b.plane_stride, s);
         ++launches;
     }
     if (e != cudaSuccess)

@@ -126,11 +126,13 @@ dd_status make_geometry(dd_plan_s *p, dd_dtype t, const dd_tiles &tl, Geometry *
     }
     const int64_t wp = widest + 16;
     const int64_t zero_bytes = ((int64_t)r.elem * r.t_cta + 16 + 15) / 16 * 16;
-    // Per stage: the staged rows (every byte phase) and the producer's
-    // offset table (one int per staged row and DM of the CTA).
+    // Per stage: the staged rows (every byte phase), the producer's offset
+    // table (one int per staged row and DM of the CTA) and a stage record;
+    // then the zero row and two mbarriers per stage.
+    const int64_t stage_bytes = (int64_t)tl.chan_per_stage * r.nph * wp;
     auto smem_for = [&](int64_t n) {
         const int64_t table = (n * tl.chan_per_stage * r.dm_cta * 4 + 15) / 16 * 16;
-        return n * tl.chan_per_stage * r.nph * wp + table + zero_bytes + 16 * n;
+        return n * stage_bytes + table + n * kStageMeta + zero_bytes + 16 * n;
     };
     int nst = 4;
     while (nst > 2 && smem_for(nst) > kMaxSmem)
@@ -141,6 +143,7 @@ dd_status make_geometry(dd_plan_s *p, dd_dtype t, const dd_tiles &tl, Geometry *
                                         " bytes of shared memory (limit 232448); use fewer "
                                         "channels per stage or fewer DMs per CTA");
     r.wp = (int)wp;
+    r.stage_bytes = (int)stage_bytes;
     r.nstages = nst;
     r.zero_bytes = (int)zero_bytes;
     r.smem = (int)smem;
