@@ -160,3 +160,77 @@ def random_filterbank(rng: np.random.Generator, nchan: int, nsamp: int, kind: st
     else:
         out[:, :nsamp] = rng.integers(0, 256, size=(nchan, nsamp), dtype=np.uint8).astype(dt)
     return out
+
+
+# ---------------------------------------------------------------------------
+# Uneven beams for one batched launch (64 beams, seed 4).  Each beam draws its
+# channel count from {256, 512, 1024, 4096}, its output length 2^k with k in
+# 14..18, its DM count from 128..2048 (DMs 0..ndm-1, step 1), and a band like
+# the small or the L-band workload: top channel 1500 MHz, 64 or 300 MHz wide
+# (foff = -bandwidth/nchan), tsamp 64 us; 1-3 pulses per beam.
+# ---------------------------------------------------------------------------
+
+@dataclass(frozen=True)
+class BeamSpec:
+    index: int
+    nchan: int
+    fch1: float
+    foff: float
+    tsamp: float
+    nsamp_out: int
+    ndm: int
+    pulses: tuple
+
+    def dm_list(self) -> np.ndarray:
+        return dm_grid(0.0, 1.0, self.ndm)
+
+    def adds(self) -> int:
+        return self.nchan * self.ndm * self.nsamp_out
+
+
+def uneven_beams(seed: int = 4, nbeams: int = 64, scale_nsamp: int = 1) -> list[BeamSpec]:
+    """The batched-beams workload; scale_nsamp > 1 divides every output length
+    (a smaller case with the same mix, for quick tests)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    out = []
+    for i in range(nbeams):
+        nchan = int(rng.choice([256, 512, 1024, 4096]))
+        nsamp = int(2 ** int(rng.integers(14, 19))) // scale_nsamp
+        ndm = int(rng.integers(128, 2049))
+        bw = float(rng.choice([64.0, 300.0]))
+        npulse = int(rng.integers(1, 4))
+        pulses = tuple(Pulse(float(rng.integers(0, ndm)), int(rng.integers(0, max(1, nsamp - 16))),
+                             int(rng.integers(1, 17)), 40.0) for _ in range(npulse))
+        out.append(BeamSpec(i, nchan, 1500.0, -bw / nchan, 64e-6, nsamp, ndm, pulses))
+    return out
+
+
+class NoisePool:
+    """Seeded pool of uint8 N(128, 16) noise (round half to even, clipped);
+    beam rows are slices of it at seeded offsets -- Gaussian values per sample
+    at memory-copy speed for multi-GB batches."""
+
+    def __init__(self, seed: int, size: int = 1 << 26):
+        rng = np.random.Generator(np.random.PCG64(seed))
+        self.pool = to_u8(rng.normal(128.0, 16.0, size=size))
+        self.rng = np.random.Generator(np.random.PCG64(seed + 1))
+
+    def rows(self, nchan: int, nsamp: int, pitch: int | None = None) -> np.ndarray:
+        pitch = nsamp if pitch is None else pitch
+        if nsamp > len(self.pool):
+            raise ValueError("row longer than the noise pool")
+        out = np.zeros((nchan, pitch), dtype=np.uint8)
+        offs = self.rng.integers(0, len(self.pool) - nsamp + 1, size=nchan)
+        for c, o in enumerate(offs):
+            out[c, :nsamp] = self.pool[o:o + nsamp]
+        return out
+
+
+def add_pulse_u8(data: np.ndarray, delays: np.ndarray, pulse: Pulse, nsamp: int) -> None:
+    """Add a square pulse to uint8 rows in place, saturating at 255."""
+    for c in range(data.shape[0]):
+        start = pulse.t + int(delays[c])
+        lo, hi = max(start, 0), min(start + pulse.width, nsamp)
+        if lo < hi:
+            seg = data[c, lo:hi].astype(np.int32) + int(pulse.amp)
+            data[c, lo:hi] = np.minimum(seg, 255).astype(np.uint8)

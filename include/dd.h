@@ -187,6 +187,42 @@ dd_status dd_execute_noalloc(dd_plan_t plan, const void *in, dd_dtype dtype, int
                              int64_t nsamp_in, float *out, int64_t out_pitch,
                              int64_t nsamp_out, void *stream);
 
+/* --- batches: uneven beams in one persistent launch ------------------------ */
+
+typedef struct dd_batch_s *dd_batch_t;
+
+/* A batch runs many beams -- each with its own plan (nchan, band, DM list)
+ * and its own buffers -- in one persistent de-dispersion launch: one CTA per
+ * SM claims (beam, DM tile, time tile) work items, largest beams first, from
+ * an atomic counter, preceded by each beam's phase-plane pre-pass.  The
+ * sequence is captured once into a CUDA graph and replayed by later
+ * dd_batch_execute calls (re-captured after dd_batch_set_io or a tile change).
+ * All beams share one tile shape (dd_batch_set_tiles / dd_batch_autotune).
+ * plans[i] must outlive the batch; the batch owns its device descriptors,
+ * counters and per-beam phase-plane scratch. */
+dd_status dd_batch_create(const dd_plan_t *plans, int nbeams, dd_dtype dtype,
+                          dd_batch_t *batch_out);
+void dd_batch_destroy(dd_batch_t batch);
+
+/* Bind beam i's device buffers (layouts and rules as dd_execute). */
+dd_status dd_batch_set_io(dd_batch_t batch, int beam, const void *in, int64_t in_pitch,
+                          int64_t nsamp_in, float *out, int64_t out_pitch, int64_t nsamp_out);
+
+/* Run every beam of the batch, asynchronously on stream. */
+dd_status dd_batch_execute(dd_batch_t batch, void *stream);
+
+dd_status dd_batch_get_tiles(dd_batch_t batch, dd_tiles *tiles_out);
+dd_status dd_batch_set_tiles(dd_batch_t batch, const dd_tiles *tiles);
+
+/* Autotuner for the batch: times each candidate tile shape that fits every
+ * beam on the bound buffers (outputs are overwritten), keeps the fastest.
+ * Same reporting as dd_autotune; synchronizes stream. */
+dd_status dd_batch_autotune(dd_batch_t batch, void *stream, int reps, dd_tune_result *results,
+                            int max_results, int *n_results);
+
+/* Synchronize stream and report the batch's device status word. */
+dd_status dd_batch_sync(dd_batch_t batch, void *stream);
+
 /* Synchronize stream and report the plan's device status word (DD_OK,
  * DD_ERR_TIMEOUT or DD_ERR_DEVICE), then clear it. */
 dd_status dd_sync(dd_plan_t plan, void *stream);

@@ -26,7 +26,9 @@ EXPORTS = [
     "dd_plan", "dd_plan_destroy", "dd_plan_maxshift", "dd_plan_nchan", "dd_plan_ndm",
     "dd_plan_dmshift", "dd_plan_get_tiles", "dd_plan_set_tiles", "dd_execute",
     "dd_execute_host", "dd_sync", "dd_profile_events", "dd_launch_count", "dd_last_error",
-    "dd_autotune", "dd_execute_noalloc",
+    "dd_autotune", "dd_execute_noalloc", "dd_batch_create", "dd_batch_destroy",
+    "dd_batch_set_io", "dd_batch_execute", "dd_batch_get_tiles", "dd_batch_set_tiles",
+    "dd_batch_autotune", "dd_batch_sync",
 ]
 
 
@@ -73,6 +75,15 @@ def _load() -> ctypes.CDLL:
         "dd_profile_events": (None, [p, p]),
         "dd_autotune": (i32, [p, p, i32, i64, i64, p, i64, i64, p, i32,
                               ctypes.POINTER(TuneResult), i32, ctypes.POINTER(i32)]),
+        "dd_batch_create": (i32, [ctypes.POINTER(p), i32, i32, ctypes.POINTER(p)]),
+        "dd_batch_destroy": (None, [p]),
+        "dd_batch_set_io": (i32, [p, i32, p, i64, i64, p, i64, i64]),
+        "dd_batch_execute": (i32, [p, p]),
+        "dd_batch_get_tiles": (i32, [p, ctypes.POINTER(Tiles)]),
+        "dd_batch_set_tiles": (i32, [p, ctypes.POINTER(Tiles)]),
+        "dd_batch_autotune": (i32, [p, p, i32, ctypes.POINTER(TuneResult), i32,
+                                    ctypes.POINTER(i32)]),
+        "dd_batch_sync": (i32, [p, p]),
         "dd_launch_count": (i64, []),
         "dd_last_error": (ctypes.c_char_p, []),
     }
@@ -244,3 +255,72 @@ class Plan:
         if stream is not None:
             h = stream if isinstance(stream, int) else stream.cuda_stream
         check(lib.dd_sync(self.handle, ctypes.c_void_p(h)))
+
+
+def _stream_handle(stream) -> int:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    return stream if isinstance(stream, int) else stream.cuda_stream
+
+
+class Batch:
+    """dd_batch: many beams (own plans and buffers) in one persistent launch,
+    replayed from a CUDA graph.  Keeps references to its plans and tensors."""
+
+    def __init__(self, plans, dtype):
+        self.plans = list(plans)
+        arr = (ctypes.c_void_p * len(self.plans))(*[pl.handle.value for pl in self.plans])
+        h = ctypes.c_void_p()
+        check(lib.dd_batch_create(arr, len(self.plans), dtype_code(dtype), ctypes.byref(h)))
+        self._h = h
+        self._keep = {}
+
+    @property
+    def handle(self):
+        if self._h is None:
+            raise ValueError("batch destroyed")
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None) is not None:
+            lib.dd_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_io(self, beam: int, inp, out, nsamp_in: int | None = None,
+               nsamp_out: int | None = None):
+        """Bind torch CUDA tensors inp [nchan][pitch] and out [ndm][pitch] to a beam."""
+        nsamp_in = inp.shape[1] if nsamp_in is None else nsamp_in
+        nsamp_out = out.shape[1] if nsamp_out is None else nsamp_out
+        check(lib.dd_batch_set_io(self.handle, beam, ctypes.c_void_p(inp.data_ptr()),
+                                  inp.stride(0), nsamp_in, ctypes.c_void_p(out.data_ptr()),
+                                  out.stride(0), nsamp_out))
+        self._keep[beam] = (inp, out)
+
+    def execute(self, stream=None):
+        check(lib.dd_batch_execute(self.handle, ctypes.c_void_p(_stream_handle(stream))))
+
+    def sync(self, stream=None):
+        check(lib.dd_batch_sync(self.handle, ctypes.c_void_p(_stream_handle(stream))))
+
+    def get_tiles(self) -> tuple:
+        t = Tiles()
+        check(lib.dd_batch_get_tiles(self.handle, ctypes.byref(t)))
+        return t.as_tuple()
+
+    def set_tiles(self, dm_per_thread, dm_warps, time_warps, chan_per_stage, words_per_thread=8):
+        t = Tiles(dm_per_thread, dm_warps, time_warps, chan_per_stage, words_per_thread)
+        check(lib.dd_batch_set_tiles(self.handle, ctypes.byref(t)))
+
+    def autotune(self, stream=None, reps: int = 1) -> list:
+        res = (TuneResult * 256)()
+        n = ctypes.c_int(0)
+        check(lib.dd_batch_autotune(self.handle, ctypes.c_void_p(_stream_handle(stream)), reps,
+                                    res, 256, ctypes.byref(n)))
+        return [(res[i].tiles.as_tuple(), float(res[i].ms)) for i in range(min(n.value, 256))]

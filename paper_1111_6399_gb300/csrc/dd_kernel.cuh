@@ -691,9 +691,19 @@ __global__ void __launch_bounds__(32 * (max_consumer_warps(DT, NW) + 1), 1)
 template <int ELEM, int DT, int NW>
 cudaError_t launch_one(const KArgs &a, unsigned grid, int threads, int smem, cudaStream_t s) {
     auto k = dedisperse_kernel<ELEM, DT, NW>;
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e != cudaSuccess)
-        return e;
+    // Raise the dynamic shared-memory limit only when a launch needs more than
+    // before (so a launch inside a stream capture never changes attributes
+    // after an eager launch of the same shape).
+    static int configured[64] = {0};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    int &conf = configured[dev & 63];
+    if (smem > conf) {
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess)
+            return e;
+        conf = smem;
+    }
     k<<<grid, threads, smem, s>>>(a);
     return cudaGetLastError();
 }
