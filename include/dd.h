@@ -223,6 +223,65 @@ dd_status dd_batch_autotune(dd_batch_t batch, void *stream, int reps, dd_tune_re
 /* Synchronize stream and report the batch's device status word. */
 dd_status dd_batch_sync(dd_batch_t batch, void *stream);
 
+/* --- serving: streaming beams, continuous batching ------------------------- */
+
+typedef struct dd_server_s *dd_server_t;
+typedef uint64_t dd_ticket;
+
+typedef struct dd_server_stats {
+    int64_t submitted;       /* blocks accepted by dd_submit                   */
+    int64_t completed;       /* blocks whose result is in the caller's buffer  */
+    int64_t rejected_busy;   /* dd_submit calls that returned DD_ERR_BUSY      */
+    int64_t batches;         /* batched launches issued                        */
+    double p50_ms, p99_ms, max_ms;  /* submit -> result latency of completed blocks */
+    double mean_batch;       /* mean blocks per batched launch                  */
+    int slots;               /* device slots (blocks in flight at most)         */
+    int64_t device_bytes;    /* device memory held (slots + beam tails)         */
+} dd_server_stats;
+
+/* A server de-disperses streams of blocks from many beams (the real-time
+ * search of Sec. 1-2).  Every beam keeps the last maxshift samples of each
+ * channel on the device (its overlap tail), so block k is processed as
+ * [tail | block] and yields the outputs of stream samples
+ * [k*B - maxshift, (k+1)*B - maxshift) (block 0: [0, B - maxshift)), B the
+ * beam's block length.  A worker thread batches blocks of different beams
+ * that are ready (previous block's tail in place) into one persistent launch
+ * as device slots free up, while later blocks are being copied in: continuous
+ * batching.  Device memory = slots + tails, bounded by hbm_budget_bytes; the
+ * number of slots is min(max_inflight, what the budget allows after tails).
+ * Blocks wait in pinned host staging (2 x slots buffers); dd_submit returns
+ * DD_ERR_BUSY when none is free. */
+dd_status dd_server_create(size_t hbm_budget_bytes, int max_inflight, dd_dtype dtype,
+                           dd_server_t *server_out);
+
+/* Register a streaming beam (plan must outlive the server).  block_nsamp B
+ * must exceed the plan's maxshift.  Beams must be added before the first
+ * dd_submit. */
+dd_status dd_server_add_beam(dd_server_t server, dd_plan_t plan, int64_t block_nsamp,
+                             int *beam_id_out);
+
+/* Queue the next block of a beam: block_host holds nchan rows of B samples,
+ * in_pitch elements apart (copied before return).  out_host receives ndm rows
+ * (out_pitch floats apart, >= B) of the block's outputs when dd_poll reports
+ * DD_OK; it must stay valid until then (pinned memory lets the copy overlap).
+ * DD_ERR_BUSY: no staging buffer free right now (retry later). */
+dd_status dd_submit(dd_server_t server, int beam_id, const void *block_host, int64_t in_pitch,
+                    float *out_host, int64_t out_pitch, dd_ticket *ticket_out);
+
+/* DD_OK once the block's outputs are in out_host (first_t: stream sample of
+ * out row column 0; nsamp: columns written), DD_PENDING while in flight,
+ * DD_ERR_INVALID for an unknown or already collected ticket, another error if
+ * the block failed.  A ticket is collected by the first DD_OK (or error). */
+dd_status dd_poll(dd_server_t server, dd_ticket ticket, int64_t *first_t, int64_t *nsamp);
+
+/* Wait (up to timeout_ms) until every submitted block has completed. */
+dd_status dd_server_drain(dd_server_t server, int64_t timeout_ms);
+
+dd_status dd_server_get_stats(dd_server_t server, dd_server_stats *stats_out);
+
+/* Stop the worker threads (after draining in-flight blocks) and free all. */
+dd_status dd_server_destroy(dd_server_t server);
+
 /* Synchronize stream and report the plan's device status word (DD_OK,
  * DD_ERR_TIMEOUT or DD_ERR_DEVICE), then clear it. */
 dd_status dd_sync(dd_plan_t plan, void *stream);

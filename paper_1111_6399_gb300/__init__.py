@@ -5,8 +5,9 @@ include/dd.h); this package is its thin Python binding.  Importing it loads
 the library and raises ImportError if it has not been built
 (``python __graft_entry__.py``).
 """
-from ._binding import (DD_F16, DD_F32, DD_U8, Batch, DDError, Plan, Tiles, check, dtype_code,
+from ._binding import (DD_F16, DD_F32, DD_U8, Batch, DDError, Plan, Server, Tiles, check,
+                       dtype_code,
                        elem_size, launch_count, lib, profile_events, warp_span)
 
-__all__ = ["Plan", "Batch", "Tiles", "DDError", "DD_U8", "DD_F16", "DD_F32", "check", "dtype_code",
+__all__ = ["Plan", "Batch", "Server", "Tiles", "DDError", "DD_U8", "DD_F16", "DD_F32", "check", "dtype_code",
            "elem_size", "warp_span", "launch_count", "profile_events", "lib"]

@@ -28,7 +28,8 @@ EXPORTS = [
     "dd_execute_host", "dd_sync", "dd_profile_events", "dd_launch_count", "dd_last_error",
     "dd_autotune", "dd_execute_noalloc", "dd_batch_create", "dd_batch_destroy",
     "dd_batch_set_io", "dd_batch_execute", "dd_batch_get_tiles", "dd_batch_set_tiles",
-    "dd_batch_autotune", "dd_batch_sync",
+    "dd_batch_autotune", "dd_batch_sync", "dd_server_create", "dd_server_add_beam",
+    "dd_submit", "dd_poll", "dd_server_drain", "dd_server_get_stats", "dd_server_destroy",
 ]
 
 
@@ -46,6 +47,17 @@ class Tiles(ctypes.Structure):
     def as_tuple(self):
         return (self.dm_per_thread, self.dm_warps, self.time_warps, self.chan_per_stage,
                 self.words_per_thread)
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64),
+                ("rejected_busy", ctypes.c_int64), ("batches", ctypes.c_int64),
+                ("p50_ms", ctypes.c_double), ("p99_ms", ctypes.c_double),
+                ("max_ms", ctypes.c_double), ("mean_batch", ctypes.c_double),
+                ("slots", ctypes.c_int), ("device_bytes", ctypes.c_int64)]
+
+    def as_dict(self):
+        return {n: getattr(self, n) for n, _ in self._fields_}
 
 
 class TuneResult(ctypes.Structure):
@@ -84,6 +96,13 @@ def _load() -> ctypes.CDLL:
         "dd_batch_autotune": (i32, [p, p, i32, ctypes.POINTER(TuneResult), i32,
                                     ctypes.POINTER(i32)]),
         "dd_batch_sync": (i32, [p, p]),
+        "dd_server_create": (i32, [ctypes.c_size_t, i32, i32, ctypes.POINTER(p)]),
+        "dd_server_add_beam": (i32, [p, p, i64, ctypes.POINTER(i32)]),
+        "dd_submit": (i32, [p, i32, p, i64, p, i64, ctypes.POINTER(ctypes.c_uint64)]),
+        "dd_poll": (i32, [p, ctypes.c_uint64, ctypes.POINTER(i64), ctypes.POINTER(i64)]),
+        "dd_server_drain": (i32, [p, i64]),
+        "dd_server_get_stats": (i32, [p, ctypes.POINTER(ServerStats)]),
+        "dd_server_destroy": (i32, [p]),
         "dd_launch_count": (i64, []),
         "dd_last_error": (ctypes.c_char_p, []),
     }
@@ -324,3 +343,75 @@ class Batch:
         check(lib.dd_batch_autotune(self.handle, ctypes.c_void_p(_stream_handle(stream)), reps,
                                     res, 256, ctypes.byref(n)))
         return [(res[i].tiles.as_tuple(), float(res[i].ms)) for i in range(min(n.value, 256))]
+
+
+class Server:
+    """dd_server: streaming blocks of many beams, continuous batching.
+    Host buffers are numpy arrays (or CPU torch tensors); the server keeps a
+    reference to every out buffer until its ticket is collected."""
+
+    def __init__(self, hbm_budget_bytes: int, max_inflight: int, dtype="u8"):
+        h = ctypes.c_void_p()
+        check(lib.dd_server_create(int(hbm_budget_bytes), int(max_inflight), dtype_code(dtype),
+                                   ctypes.byref(h)))
+        self._h = h
+        self._plans = []
+        self._outs = {}
+
+    @property
+    def handle(self):
+        if self._h is None:
+            raise ValueError("server destroyed")
+        return self._h
+
+    def add_beam(self, plan, block_nsamp: int) -> int:
+        bid = ctypes.c_int(-1)
+        check(lib.dd_server_add_beam(self.handle, plan.handle, int(block_nsamp),
+                                     ctypes.byref(bid)))
+        self._plans.append(plan)
+        return bid.value
+
+    def submit(self, beam: int, block, out):
+        """Queue a block ([nchan][>=B] host array); returns a ticket, or None if busy."""
+        b = block.numpy() if hasattr(block, "numpy") and not isinstance(block, np.ndarray) else block
+        o = out.numpy() if hasattr(out, "numpy") and not isinstance(out, np.ndarray) else out
+        if o.dtype != np.float32 or o.strides[1] != 4 or b.strides[1] != b.itemsize:
+            raise ValueError("block rows must be contiguous; out must be float32 rows")
+        t = ctypes.c_uint64(0)
+        st = lib.dd_submit(self.handle, beam, b.ctypes.data, b.strides[0] // b.itemsize,
+                           o.ctypes.data, o.strides[0] // 4, ctypes.byref(t))
+        if st == DD_ERR_BUSY:
+            return None
+        check(st)
+        self._outs[t.value] = out
+        return t.value
+
+    def poll(self, ticket: int):
+        """None while pending, else (first_t, nsamp)."""
+        f, n = ctypes.c_int64(0), ctypes.c_int64(0)
+        st = lib.dd_poll(self.handle, ctypes.c_uint64(ticket), ctypes.byref(f), ctypes.byref(n))
+        if st == DD_PENDING:
+            return None
+        self._outs.pop(ticket, None)
+        check(st)
+        return f.value, n.value
+
+    def drain(self, timeout_ms: int = 60000):
+        check(lib.dd_server_drain(self.handle, int(timeout_ms)))
+
+    def stats(self) -> dict:
+        s = ServerStats()
+        check(lib.dd_server_get_stats(self.handle, ctypes.byref(s)))
+        return s.as_dict()
+
+    def close(self):
+        if getattr(self, "_h", None) is not None:
+            st = lib.dd_server_destroy(self._h)
+            self._h = None
+            check(st)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
