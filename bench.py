@@ -155,6 +155,162 @@ def cpu_oracle_sample(w: fb.Workload, budget_s: float = 12.0):
                       f"({adds:.3g} adds, {dt:.1f} s, OpenMP over DMs)"}
 
 
+def _plan_delays(table: np.ndarray, pulses):
+    return [np.trunc((np.float32(p.dm) * table).astype(np.float32)).astype(np.int64)
+            for p in pulses]
+
+
+def batch_section(dd, torch, dev, steps: int):
+    """64 uneven beams: one persistent launch replayed from a CUDA graph versus
+    one plain single-beam launch per beam, on the same device buffers."""
+    specs = fb.uneven_beams()
+    pool = fb.NoisePool(4)
+    plans, ins, outs_b, outs_p, nins = [], [], [], [], []
+    for sp in specs:
+        plan = dd.Plan(sp.nchan, sp.fch1, sp.foff, sp.tsamp, sp.dm_list())
+        nin = sp.nsamp_out + plan.maxshift
+        data = pool.rows(sp.nchan, nin, (nin + 15) // 16 * 16)
+        for p, dl in zip(sp.pulses, _plan_delays(plan.dmshift(), sp.pulses)):
+            fb.add_pulse_u8(data, dl, p, nin)
+        plans.append(plan)
+        nins.append(nin)
+        ins.append(torch.from_numpy(data).to(dev))
+        outs_b.append(torch.empty((sp.ndm, (sp.nsamp_out + 3) // 4 * 4), device=dev))
+        outs_p.append(torch.empty_like(outs_b[-1]))
+    batch = dd.Batch(plans, "u8")
+    for i, sp in enumerate(specs):
+        batch.set_io(i, ins[i], outs_b[i], nsamp_in=nins[i], nsamp_out=sp.nsamp_out)
+    stream = torch.cuda.current_stream(dev)
+    for _ in range(3):
+        batch.execute(stream)           # eager run + capture, then replays
+        for i, sp in enumerate(specs):
+            plans[i].execute(ins[i], outs_p[i], nsamp_in=nins[i], nsamp_out=sp.nsamp_out,
+                             stream=stream)
+    batch.sync(stream)
+    reps = max(2, min(steps, 5))
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    e[0].record(stream)
+    for _ in range(reps):
+        batch.execute(stream)
+    e[1].record(stream)
+    for _ in range(reps):
+        for i, sp in enumerate(specs):
+            plans[i].execute(ins[i], outs_p[i], nsamp_in=nins[i], nsamp_out=sp.nsamp_out,
+                             stream=stream)
+    e[2].record(stream)
+    torch.cuda.synchronize(dev)
+    t_batch = e[0].elapsed_time(e[1]) / reps / 1e3
+    t_plain = e[1].elapsed_time(e[2]) / reps / 1e3
+    same = all(torch.equal(outs_b[i][:, :sp.nsamp_out], outs_p[i][:, :sp.nsamp_out])
+               for i, sp in enumerate(specs))
+    adds = sum(sp.adds() for sp in specs)
+    res = {"workload": "64 uneven beams (nchan 256-4096, nsamp 2^14-2^18, ndm 128-2048)",
+           "adds": adds, "batched_adds_per_s": adds / t_batch,
+           "per_beam_adds_per_s": adds / t_plain, "speedup": t_plain / t_batch,
+           "batched_ms": t_batch * 1e3, "per_beam_ms": t_plain * 1e3,
+           "identical_outputs": bool(same), "tiles": batch.get_tiles(),
+           "launch": "phase planes per beam + one persistent kernel, CUDA graph replay"}
+    del ins, outs_b, outs_p
+    batch.close()
+    torch.cuda.empty_cache()
+    return res
+
+
+def serving_section(dd, torch, dev, seconds: float = 8.0, speed: float = 1.25):
+    """128 streaming L-band beams (1024 channels, 1024 DMs, blocks of 65536
+    samples = 4.194 s) served with continuous batching: Poisson arrivals at
+    `speed` x the aggregate real-time rate for `seconds`, then a saturating
+    phase (blocks submitted as fast as the server accepts them)."""
+    w = fb.LBAND
+    B, nbeams = 65536, 128
+    plan = dd.Plan(w.nchan, w.fch1, w.foff, w.tsamp, w.dm_list())
+    block_s = B * w.tsamp
+    rng = np.random.default_rng(5)
+    pool = fb.NoisePool(5)
+    blocks = [pool.rows(w.nchan, B) for _ in range(4)]
+    slots = 8
+    srv = dd.Server(24 << 30, slots, "u8")
+    ids = [srv.add_beam(plan, B) for _ in range(nbeams)]
+    outs = [torch.empty((w.ndm, B), dtype=torch.float32).pin_memory() for _ in range(2 * slots)]
+    free = list(range(len(outs)))
+    pending = {}
+
+    def reap():
+        for t in list(pending):
+            r = srv.poll(t)
+            if r is not None:
+                free.append(pending.pop(t))
+
+    def submit(beam, k):
+        while not free:
+            reap()
+            time.sleep(0.0002)
+        o = free.pop()
+        t = srv.submit(ids[beam], blocks[k % 4], outs[o])
+        if t is None:
+            free.append(o)
+            return False
+        pending[t] = o
+        return True
+
+    # real-time phase: aggregate Poisson arrivals, beams in turn
+    rate = speed * nbeams / block_s
+    t0 = time.perf_counter()
+    t_next, n, late = 0.0, 0, 0
+    kblock = [0] * nbeams
+    while True:
+        now = time.perf_counter() - t0
+        if now >= seconds:
+            break
+        if now >= t_next:
+            b = n % nbeams
+            if submit(b, kblock[b]):
+                kblock[b] += 1
+                n += 1
+            else:
+                late += 1
+            t_next += rng.exponential(1.0 / rate)
+        else:
+            reap()
+            time.sleep(min(0.0005, t_next - now))
+    srv.drain()
+    reap()
+    st_rt = srv.stats()
+    wall_rt = time.perf_counter() - t0
+    # saturating phase
+    done0 = st_rt["completed"]
+    t1 = time.perf_counter()
+    m = 0
+    while m < 96:
+        b = (n + m) % nbeams
+        if submit(b, kblock[b]):
+            kblock[b] += 1
+            m += 1
+        else:
+            reap()
+            time.sleep(0.0002)
+    srv.drain()
+    reap()
+    wall_sat = time.perf_counter() - t1
+    st = srv.stats()
+    srv.close()
+    sat_blocks = st["completed"] - done0
+    adds_block = w.nchan * w.ndm * B
+    return {"workload": "128 streaming beams x (1024 ch, 1024 DMs, 65536-sample blocks)",
+            "arrivals": f"Poisson at {speed}x aggregate real time for {seconds:.0f} s",
+            "blocks_real_time": st_rt["completed"], "busy_rejections": st_rt["rejected_busy"],
+            "late_arrivals": late,
+            "p50_ms": st_rt["p50_ms"], "p99_ms": st_rt["p99_ms"], "max_ms": st_rt["max_ms"],
+            "block_duration_ms": block_s * 1e3,
+            "p99_below_block_duration": st_rt["p99_ms"] < block_s * 1e3,
+            "mean_batch": st_rt["mean_batch"], "slots": st_rt["slots"],
+            "device_bytes": st_rt["device_bytes"],
+            "saturated_blocks_per_s": sat_blocks / wall_sat,
+            "saturated_adds_per_s": sat_blocks * adds_block / wall_sat,
+            "real_time_beams_sustained": sat_blocks / wall_sat * block_s,
+            "wall_s": wall_rt + wall_sat}
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -309,6 +465,12 @@ def run_ours(args, w):
     }
     if clocks:
         line["clocks"] = clocks
+    del x, out, h_in, h_out
+    torch.cuda.empty_cache()
+    if not args.no_batch and world == 1:
+        line["batch"] = batch_section(dd, torch, dev, args.steps)
+    if not args.no_serve and world == 1:
+        line["serving"] = serving_section(dd, torch, dev)
     if not args.no_cpu:
         line["cpu_baseline"] = cpu_oracle_sample(w)
     print(json.dumps(line), flush=True)
@@ -325,6 +487,8 @@ def main():
     ap.add_argument("--workload", default="lband", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-tune", action="store_true", help="use the plan's default tile shape")
+    ap.add_argument("--no-batch", action="store_true", help="skip the 64-beam batch section")
+    ap.add_argument("--no-serve", action="store_true", help="skip the serving section")
     ap.add_argument("--tiles", default="", help="fixed tile shape dthr,dm_warps,time_warps,cstage")
     args = ap.parse_args()
     w = WORKLOADS[args.workload]
