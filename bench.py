@@ -160,7 +160,7 @@ def _plan_delays(table: np.ndarray, pulses):
             for p in pulses]
 
 
-def batch_section(dd, torch, dev, steps: int):
+def batch_section(dd, torch, dev, steps: int, tiles=None):
     """64 uneven beams: one persistent launch replayed from a CUDA graph versus
     one plain single-beam launch per beam, on the same device buffers."""
     specs = fb.uneven_beams()
@@ -180,6 +180,13 @@ def batch_section(dd, torch, dev, steps: int):
     batch = dd.Batch(plans, "u8")
     for i, sp in enumerate(specs):
         batch.set_io(i, ins[i], outs_b[i], nsamp_in=nins[i], nsamp_out=sp.nsamp_out)
+    if tiles is not None:  # the headline's tuned shape, for the batch and every single beam
+        try:
+            batch.set_tiles(*tiles)
+            for pl in plans:
+                pl.set_tiles("u8", *tiles)
+        except dd.DDError:
+            pass
     stream = torch.cuda.current_stream(dev)
     for _ in range(3):
         batch.execute(stream)           # eager run + capture, then replays
@@ -357,13 +364,16 @@ def run_ours(args, w):
     plan = dd.Plan(w.nchan, w.fch1, w.foff, w.tsamp, w.dm_list())
     S = plan.maxshift
     host, nin = make_input(w, plan.dmshift(), S)
+    dt = args.dtype
+    if dt != "u8":  # the same integer noise stored as FP16/FP32, pitch kept 16-byte aligned
+        host = host.astype(np.float16 if dt == "f16" else np.float32)
     x = torch.from_numpy(host).to(dev)
     out = torch.empty((w.ndm, w.nsamp_out), dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream(dev)
 
     tune = None
     if args.tiles:
-        plan.set_tiles("u8", *[int(v) for v in args.tiles.split(",")])
+        plan.set_tiles(dt, *[int(v) for v in args.tiles.split(",")])
     elif not args.no_tune:
         tune = plan.autotune(x, out, nsamp_in=nin, stream=stream, reps=2)
         if rank == 0:
@@ -441,9 +451,9 @@ def run_ours(args, w):
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+        "scaling": "weak", "vs_baseline": None, "dtype": dt, "data": "synthetic",
         "config": {"workload": w.name, "nchan": w.nchan, "ndm": w.ndm,
-                   "nsamp_out": w.nsamp_out, "maxshift": S, "tiles": plan.get_tiles("u8"),
+                   "nsamp_out": w.nsamp_out, "maxshift": S, "tiles": plan.get_tiles(dt),
                    "tiles_from": "fixed" if args.tiles else ("default" if args.no_tune
                                                              else "autotuner"),
                    "l2": "inputs larger than L2 (151 MB in + 537 MB out per step)",
@@ -452,13 +462,14 @@ def run_ours(args, w):
                      "unit": "Tadd/s", "frac": achieved / peak_adds, "traffic": None,
                      "peak_source": f"{SM_COUNT} SMs x {ADD_LANES_PER_SM} lanes x "
                                     f"{pk.get('sm_max_mhz', 2070.0):.0f} MHz ({pk_kind} max clock)",
-                     "kernel": "dedisperse_kernel<1,%d,%d>" % (plan.get_tiles("u8")[0],
-                                                                 plan.get_tiles("u8")[4]),
+                     "kernel": "dedisperse_kernel<%d,%d,%d>" % (
+                         {"u8": 1, "f16": 2, "f32": 4}[dt], plan.get_tiles(dt)[0],
+                         plan.get_tiles(dt)[4]),
                      "kernel_ms": kernel_ms,
                      "step_ms": step_ms},
         "real_time_factor": w.duration_s() / (step_ms / 1e3),
         "e2e": {"value": adds * world / e2e_s, "unit": UNIT,
-                "h2d_bytes_per_step": int(w.nchan * nin),
+                "h2d_bytes_per_step": int(w.nchan * nin * host.itemsize),
                 "d2h_bytes_per_step": int(w.ndm * w.nsamp_out * 4)},
         "gpu_launches": launches,
         "wall_s_timed": wall,
@@ -468,7 +479,8 @@ def run_ours(args, w):
     del x, out, h_in, h_out
     torch.cuda.empty_cache()
     if not args.no_batch and world == 1:
-        line["batch"] = batch_section(dd, torch, dev, args.steps)
+        line["batch"] = batch_section(dd, torch, dev, args.steps,
+                                      plan.get_tiles(dt) if dt == "u8" else None)
     if not args.no_serve and world == 1:
         line["serving"] = serving_section(dd, torch, dev)
     if not args.no_cpu:
@@ -487,6 +499,8 @@ def main():
     ap.add_argument("--workload", default="lband", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-tune", action="store_true", help="use the plan's default tile shape")
+    ap.add_argument("--dtype", default="u8", choices=["u8", "f16", "f32"],
+                    help="storage type of the beam (the same integer noise)")
     ap.add_argument("--no-batch", action="store_true", help="skip the 64-beam batch section")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving section")
     ap.add_argument("--tiles", default="", help="fixed tile shape dthr,dm_warps,time_warps,cstage")
