@@ -318,6 +318,17 @@ def serving_section(dd, torch, dev, seconds: float = 8.0, speed: float = 1.25):
             "wall_s": wall_rt + wall_sat}
 
 
+def max_over_ranks(value: float, dist, device) -> float:
+    """Max of a per-rank timing over all ranks (a timing reduction only: the
+    ranks de-disperse independent beams and exchange no data)."""
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -419,10 +430,7 @@ def run_ours(args, w):
     kernel_ms = sum(a.elapsed_time(b) for a, b in kev) / len(kev)
     step_ms = sum(per_step_ms) / len(per_step_ms)
     total_ms = sum(per_step_ms)
-    if dist is not None:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(total_ms, dist, dev)
     adds = w.adds()
     value = adds * world * args.steps / (total_ms / 1e3)
 
@@ -436,10 +444,7 @@ def run_ours(args, w):
     for _ in range(e2e_steps):
         plan.execute_host(h_in, h_out, nsamp_in=nin)
     e2e_s = (time.perf_counter() - t) / e2e_steps
-    if dist is not None:
-        tt = torch.tensor([e2e_s], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e2e_s = float(tt.item())
+    e2e_s = max_over_ranks(e2e_s, dist, dev)
 
     if rank != 0:
         dist.destroy_process_group()
@@ -456,7 +461,8 @@ def run_ours(args, w):
                    "nsamp_out": w.nsamp_out, "maxshift": S, "tiles": plan.get_tiles(dt),
                    "tiles_from": "fixed" if args.tiles else ("default" if args.no_tune
                                                              else "autotuner"),
-                   "l2": "inputs larger than L2 (151 MB in + 537 MB out per step)",
+                   "l2": "inputs larger than L2 (%.0f MB in + %.0f MB out per step, L2 126 MB)"
+                         % (w.nchan * nin * host.itemsize / 1e6, w.ndm * w.nsamp_out * 4 / 1e6),
                    "parallelism": f"replicas{world}" if world > 1 else "single-gpu"},
         "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_adds / 1e12,
                      "unit": "Tadd/s", "frac": achieved / peak_adds, "traffic": None,

@@ -293,6 +293,13 @@ dd_status dd_sync(dd_plan_t plan, void *stream);
  * NULLs to clear. */
 void dd_profile_events(void *start_event, void *stop_event);
 
+/* Self-test of the kernels' bounded waits: one CTA waits, through the same
+ * wait routine the de-dispersion kernel uses, on an mbarrier that nothing
+ * arrives on, with a limit of limit_ns (1 us .. 2 s).  Returns DD_ERR_TIMEOUT
+ * when the wait gave up and reported it as designed (no fault, no hang);
+ * synchronizes stream. */
+dd_status dd_selftest_wait_timeout(int64_t limit_ns, void *stream);
+
 /* Kernel launches made by this process so far (all entry points). */
 int64_t dd_launch_count(void);
 

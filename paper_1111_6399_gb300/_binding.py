@@ -30,6 +30,7 @@ EXPORTS = [
     "dd_batch_set_io", "dd_batch_execute", "dd_batch_get_tiles", "dd_batch_set_tiles",
     "dd_batch_autotune", "dd_batch_sync", "dd_server_create", "dd_server_add_beam",
     "dd_submit", "dd_poll", "dd_server_drain", "dd_server_get_stats", "dd_server_destroy",
+    "dd_selftest_wait_timeout",
 ]
 
 
@@ -103,6 +104,7 @@ def _load() -> ctypes.CDLL:
         "dd_server_drain": (i32, [p, i64]),
         "dd_server_get_stats": (i32, [p, ctypes.POINTER(ServerStats)]),
         "dd_server_destroy": (i32, [p]),
+        "dd_selftest_wait_timeout": (i32, [i64, p]),
         "dd_launch_count": (i64, []),
         "dd_last_error": (ctypes.c_char_p, []),
     }

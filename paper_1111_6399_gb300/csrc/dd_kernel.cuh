@@ -107,17 +107,18 @@ __device__ __forceinline__ bool mbar_try(uint32_t mb, uint32_t parity) {
 }
 
 // Bounded wait for the completion of the phase with the given parity.
-__device__ __noinline__ bool mbar_wait_slow(uint32_t mb, uint32_t parity) {
+__device__ __noinline__ bool mbar_wait_slow(uint32_t mb, uint32_t parity, uint64_t limit_ns) {
     const uint64_t t0 = global_ns();
     while (!mbar_try(mb, parity)) {
-        if (global_ns() - t0 > kWaitLimitNs)
+        if (global_ns() - t0 > limit_ns)
             return false;
     }
     return true;
 }
 
-__device__ __forceinline__ bool mbar_wait(uint32_t mb, uint32_t parity) {
-    return mbar_try(mb, parity) || mbar_wait_slow(mb, parity);
+__device__ __forceinline__ bool mbar_wait(uint32_t mb, uint32_t parity,
+                                          uint64_t limit_ns = kWaitLimitNs) {
+    return mbar_try(mb, parity) || mbar_wait_slow(mb, parity, limit_ns);
 }
 
 __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t bytes,

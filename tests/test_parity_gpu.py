@@ -275,3 +275,19 @@ def test_autotuner_picks_a_shape_that_stays_bit_exact(dd, oracle_lib):
     got = _run(dd, plan, data, nin, 3000)
     want = oracle_lib.dedisperse(np.ascontiguousarray(data[:, :nin]), table, dms, 3000)
     assert np.array_equal(got, want)
+
+
+def test_bounded_wait_runs_out_and_reports_without_fault(dd):
+    """A wait on an mbarrier nothing arrives on gives up after its limit and
+    reports DD_ERR_TIMEOUT; the context stays usable afterwards."""
+    import time
+    t = time.perf_counter()
+    st = dd.lib.dd_selftest_wait_timeout(50_000_000, None)   # 50 ms
+    assert st == dd.DD_ERR_TIMEOUT if hasattr(dd, "DD_ERR_TIMEOUT") else st == -5
+    assert time.perf_counter() - t < 5.0
+    plan = dd.Plan(16, 1400.0, -1.0, 1e-4, [0.0, 2.0])
+    x = torch.ones((16, 1024), dtype=torch.uint8, device="cuda")
+    out = torch.empty((2, 512), device="cuda")
+    plan.execute(x, out)
+    plan.sync()
+    assert torch.all(out == 16.0)
