@@ -274,6 +274,11 @@ dd_status dd_submit(dd_server_t server, int beam_id, const void *block_host, int
  * the block failed.  A ticket is collected by the first DD_OK (or error). */
 dd_status dd_poll(dd_server_t server, dd_ticket ticket, int64_t *first_t, int64_t *nsamp);
 
+/* Batching window: when ready blocks fill fewer than the free slots, the
+ * worker waits up to `microseconds` for more to arrive before launching
+ * (0, the default, launches at once).  Trades latency for larger batches. */
+dd_status dd_server_set_batch_window(dd_server_t server, int64_t microseconds);
+
 /* Wait (up to timeout_ms) until every submitted block has completed. */
 dd_status dd_server_drain(dd_server_t server, int64_t timeout_ms);
 

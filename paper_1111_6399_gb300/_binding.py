@@ -30,7 +30,7 @@ EXPORTS = [
     "dd_batch_set_io", "dd_batch_execute", "dd_batch_get_tiles", "dd_batch_set_tiles",
     "dd_batch_autotune", "dd_batch_sync", "dd_server_create", "dd_server_add_beam",
     "dd_submit", "dd_poll", "dd_server_drain", "dd_server_get_stats", "dd_server_destroy",
-    "dd_selftest_wait_timeout",
+    "dd_selftest_wait_timeout", "dd_server_set_batch_window",
 ]
 
 
@@ -102,6 +102,7 @@ def _load() -> ctypes.CDLL:
         "dd_submit": (i32, [p, i32, p, i64, p, i64, ctypes.POINTER(ctypes.c_uint64)]),
         "dd_poll": (i32, [p, ctypes.c_uint64, ctypes.POINTER(i64), ctypes.POINTER(i64)]),
         "dd_server_drain": (i32, [p, i64]),
+        "dd_server_set_batch_window": (i32, [p, i64]),
         "dd_server_get_stats": (i32, [p, ctypes.POINTER(ServerStats)]),
         "dd_server_destroy": (i32, [p]),
         "dd_selftest_wait_timeout": (i32, [i64, p]),
@@ -397,6 +398,9 @@ class Server:
         self._outs.pop(ticket, None)
         check(st)
         return f.value, n.value
+
+    def set_batch_window(self, microseconds: int):
+        check(lib.dd_server_set_batch_window(self.handle, int(microseconds)))
 
     def drain(self, timeout_ms: int = 60000):
         check(lib.dd_server_drain(self.handle, int(timeout_ms)))

@@ -114,6 +114,7 @@ struct dd_server_s {
     dd_ticket next_ticket = 1;
     std::thread worker, completer;
     bool stop = false;
+    int64_t window_us = 0;  // how long a partly filled batch waits for more blocks
     int64_t submitted = 0, completed = 0, rejected = 0, batches = 0, batched_blocks = 0;
     std::vector<double> lat_ms;
 };
@@ -405,6 +406,19 @@ void worker_main(dd_server_s *v) {
         v->cv_work.wait(lk, [&]() { return v->stop || collect(); });
         if (v->stop && rs.empty())
             break;
+        if (v->window_us > 0 && !v->stop) {
+            // Let more ready blocks join until the slots are full or the window ends.
+            int nfree = 0;
+            for (const Slot &sl : v->slots)
+                nfree += sl.busy ? 0 : 1;
+            const auto until = Clock::now() + std::chrono::microseconds(v->window_us);
+            while (!v->stop && (int)rs.size() < nfree &&
+                   v->cv_work.wait_until(lk, until) != std::cv_status::timeout)
+                collect();
+            collect();
+            if (rs.empty())
+                continue;
+        }
         for (size_t i = 0; i < rs.size(); ++i) {
             SrvReq &r = *rs[i];
             v->slots[r.slot].busy = true;
@@ -619,6 +633,14 @@ dd_status dd_poll(dd_server_t v, dd_ticket t, int64_t *first_t, int64_t *nsamp) 
         return st;
     }
     return DD_PENDING;
+}
+
+dd_status dd_server_set_batch_window(dd_server_t v, int64_t microseconds) {
+    if (!v || microseconds < 0 || microseconds > 10000000)
+        return fail(DD_ERR_INVALID, "batch window must be 0..10 s");
+    std::lock_guard<std::mutex> lk(v->mu);
+    v->window_us = microseconds;
+    return DD_OK;
 }
 
 dd_status dd_server_drain(dd_server_t v, int64_t timeout_ms) {

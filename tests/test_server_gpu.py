@@ -62,8 +62,9 @@ class Stream:
                 assert np.array_equal(plane[d, t].astype(np.float64), w), f"block {k}"
 
 
-def _serve(dd, streams, budget=8 << 30, inflight=8, interleave=True):
+def _serve(dd, streams, budget=8 << 30, inflight=8, interleave=True, window_us=0):
     srv = dd.Server(budget, inflight, "u8")
+    srv.set_batch_window(window_us)
     ids = [srv.add_beam(s.plan(dd), s.B) for s in streams]
     pending = {}
     order = [(i, k) for k in range(max(s.nblocks for s in streams)) for i in range(len(streams))
@@ -109,7 +110,8 @@ def test_a_beam_served_alone_and_in_a_mix_gives_the_same_bytes(dd, oracle_lib):
     _serve(dd, [alone])
     mixed = Stream(oracle_lib, 99, 128, 64, 300.0, 3000, 4)
     others = [Stream(oracle_lib, 200 + i, 96, 50, 64.0, 2500, 4) for i in range(5)]
-    stats, _ = _serve(dd, [others[0], others[1], mixed, others[2], others[3], others[4]])
+    stats, _ = _serve(dd, [others[0], others[1], mixed, others[2], others[3], others[4]],
+                      window_us=200_000)
     assert stats["mean_batch"] > 1.0   # blocks of different beams shared launches
     for k in range(4):
         assert alone.got[k] == mixed.got[k]
