@@ -106,27 +106,21 @@ __device__ __forceinline__ bool mbar_try(uint32_t mb, uint32_t parity) {
     return ok != 0;
 }
 
-// try_wait with a suspend-time hint: the warp sleeps until the phase
-// completes or hint_ns elapse, instead of spinning on the issue slots.
-__device__ __forceinline__ bool mbar_try_sleep(uint32_t mb, uint32_t parity, uint32_t hint_ns) {
-    uint32_t ok;
-    asm volatile(
-        "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3; "
-        "selp.u32 %0, 1, 0, p; }"
-        : "=r"(ok)
-        : "r"(mb), "r"(parity), "r"(hint_ns)
-        : "memory");
-    return ok != 0;
-}
-
-// Bounded wait for the completion of the phase with the given parity.
+// Bounded wait for the completion of the phase with the given parity.  The
+// waiting warp backs off with __nanosleep (64 ns doubling to 1 us) so it does
+// not take issue slots from the warps that share its scheduler; the global
+// timer is read every 16 tries.
 __device__ __noinline__ bool mbar_wait_slow(uint32_t mb, uint32_t parity, uint64_t limit_ns) {
     const uint64_t t0 = global_ns();
-    while (!mbar_try_sleep(mb, parity, 20000u)) {
-        if (global_ns() - t0 > limit_ns)
+    uint32_t ns = 64;
+    for (uint32_t i = 1;; ++i) {
+        if (mbar_try(mb, parity))
+            return true;
+        __nanosleep(ns);
+        ns = ns < 1024u ? 2u * ns : 1024u;
+        if ((i & 15u) == 0 && global_ns() - t0 > limit_ns)
             return false;
     }
-    return true;
 }
 
 __device__ __forceinline__ bool mbar_wait(uint32_t mb, uint32_t parity,
