@@ -124,16 +124,16 @@ def make_input(w: fb.Workload, dmshift: np.ndarray, maxshift: int):
     return fb.filterbank(w.nchan, nin, w.seed, pulses, delays, pitch=pitch), nin
 
 
-def cpu_oracle_sample(w: fb.Workload, budget_s: float = 12.0):
-    """Time the oracle (checker build, DM loop over all host cores) on a bounded
-    sample of the workload: all channels, a spread of the DMs, a slice of time."""
+def prepare_oracle_sample(w: fb.Workload, budget_s: float = 12.0) -> dict:
+    """A bounded sample of the workload for the oracle (checker build, DM loop
+    over all host cores): all channels, a spread of the DMs, a slice of time,
+    sized from a short calibration run to take about budget_s."""
     import oracle
     table = oracle.dmshift(w.nchan, w.fch1, w.foff, w.tsamp)
     dms_all = w.dm_list()
     S = oracle.maxshift(table, dms_all)
     rng = np.random.default_rng(w.seed)
     cores = os.cpu_count() or 1
-    # calibrate on a short slice, then size the sample to roughly budget_s
     nsamp = min(w.nsamp_out, 4096)
     ndm = max(1, min(w.ndm, 2 * cores))
     data = rng.integers(0, 256, size=(w.nchan, nsamp + S), dtype=np.uint8)
@@ -144,15 +144,25 @@ def cpu_oracle_sample(w: fb.Workload, budget_s: float = 12.0):
     target = rate * budget_s
     ndm = int(max(1, min(w.ndm, target / (w.nchan * nsamp))))
     nsamp = int(max(1024, min(w.nsamp_out, target / (w.nchan * ndm))))
-    data = rng.integers(0, 256, size=(w.nchan, nsamp + S), dtype=np.uint8)
-    sel = dms_all[np.linspace(0, w.ndm - 1, ndm).astype(int)]
+    return {"data": rng.integers(0, 256, size=(w.nchan, nsamp + S), dtype=np.uint8),
+            "table": table, "sel": dms_all[np.linspace(0, w.ndm - 1, ndm).astype(int)],
+            "nsamp": nsamp, "ndm": ndm, "cores": cores}
+
+
+def time_oracle_sample(w: fb.Workload, prep: dict) -> dict:
+    """One timed oracle run over a prepared sample."""
+    import oracle
     t = time.perf_counter()
-    oracle.dedisperse(data, table, sel, nsamp, threads=True)
+    oracle.dedisperse(prep["data"], prep["table"], prep["sel"], prep["nsamp"], threads=True)
     dt = time.perf_counter() - t
-    adds = w.nchan * ndm * nsamp
-    return {"value": adds / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"{w.nchan} channels x {ndm} of {w.ndm} DMs x {nsamp} samples "
-                      f"({adds:.3g} adds, {dt:.1f} s, OpenMP over DMs)"}
+    adds = w.nchan * prep["ndm"] * prep["nsamp"]
+    return {"value": adds / dt, "unit": UNIT, "cores": prep["cores"], "kind": "oracle",
+            "sample": f"{w.nchan} channels x {prep['ndm']} of {w.ndm} DMs x {prep['nsamp']} "
+                      f"samples ({adds:.3g} adds, {dt:.2f} s, OpenMP over DMs)"}
+
+
+def cpu_oracle_sample(w: fb.Workload, budget_s: float = 12.0) -> dict:
+    return time_oracle_sample(w, prepare_oracle_sample(w, budget_s))
 
 
 def _plan_delays(table: np.ndarray, pulses):
@@ -216,7 +226,7 @@ def batch_section(dd, torch, dev, steps: int, tiles=None):
            "per_beam_adds_per_s": adds / t_plain, "speedup": t_plain / t_batch,
            "batched_ms": t_batch * 1e3, "per_beam_ms": t_plain * 1e3,
            "identical_outputs": bool(same), "tiles": batch.get_tiles(),
-           "launch": "phase planes per beam + one persistent kernel, CUDA graph replay"}
+           "launch": "one persistent kernel, CUDA graph replay"}
     del ins, outs_b, outs_p
     batch.close()
     torch.cuda.empty_cache()
@@ -340,11 +350,13 @@ def run_reference(args, w):
     rank, world, _ = dist_env()
     if rank != 0:
         return
-    # each step: one bounded oracle sample of the workload
+    # each step: one oracle run over the same bounded sample of the workload,
+    # sized so that the whole run takes about a minute and a half
+    prep = prepare_oracle_sample(w, budget_s=max(0.25, 90.0 / (args.warmup + args.steps)))
     vals = []
     last = None
     for i in range(args.warmup + args.steps):
-        res = cpu_oracle_sample(w, budget_s=max(2.0, 20.0 / (args.warmup + args.steps)))
+        res = time_oracle_sample(w, prep)
         if i >= args.warmup:
             vals.append(res["value"])
         last = res

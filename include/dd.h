@@ -167,16 +167,16 @@ dd_status dd_execute_host(dd_plan_t plan, const void *in_host, dd_dtype dtype,
  * The paper has no counterpart: this serves callers that cannot call
  * cudaMalloc -- code running inside an allocator or memory-pool callback,
  * real-time threads that must not take the driver's allocation locks, hosts
- * that forbid the library from owning device memory.  Everything the kernels
- * need beyond in and out (the plan's device tables, the status word, the
- * byte-phase planes of 8/16-bit input) lives in one fixed 64 MiB device array
- * inside the library, written with copies and a memset on stream; the call
- * makes no cudaMalloc/cudaFree.  Each GPU that loads the library holds that
- * array until the process exits.
- * Limit: 256 + table bytes + (phases - 1) * nchan * in_pitch * element size
- * must fit in 64 MiB (phases: 4 for uint8, 2 for FP16, 1 for FP32), i.e. about
- * 21 MB of uint8 input; a larger input returns DD_ERR_INVALID (use
- * dd_execute).  The first call on a device looks up the array's device
+ * that forbid the library from owning device memory.  Everything the kernel
+ * needs beyond in and out (the plan's device tables and the status word)
+ * lives in one fixed 1 MiB device array inside the library, written with
+ * copies and a memset on stream; the call makes no cudaMalloc/cudaFree.  Each
+ * GPU that loads the library holds that array until the process exits.
+ * Limit: 256 + the tables (4 bytes per channel and 8 per DM, the DM count
+ * rounded up to a multiple of 64 plus 64, each part rounded up to 256 bytes)
+ * must fit in 1 MiB, e.g. 4096 channels and up to about 128000 DMs; a larger
+ * plan returns DD_ERR_INVALID (use dd_execute).  The input size is not
+ * limited.  The first call on a device looks up the array's device
  * address; make that call before any stream capture.  All calls share the
  * array and a call overwrites what the last one left: calls whose GPU work
  * overlaps (other streams or threads) race and must be serialized by the
@@ -194,12 +194,12 @@ typedef struct dd_batch_s *dd_batch_t;
 /* A batch runs many beams -- each with its own plan (nchan, band, DM list)
  * and its own buffers -- in one persistent de-dispersion launch: one CTA per
  * SM claims (beam, DM tile, time tile) work items, largest beams first, from
- * an atomic counter, preceded by each beam's phase-plane pre-pass.  The
- * sequence is captured once into a CUDA graph and replayed by later
+ * an atomic counter.  The launch (and the reset of the counter before it) is
+ * captured once into a CUDA graph and replayed by later
  * dd_batch_execute calls (re-captured after dd_batch_set_io or a tile change).
  * All beams share one tile shape (dd_batch_set_tiles / dd_batch_autotune).
- * plans[i] must outlive the batch; the batch owns its device descriptors,
- * counters and per-beam phase-plane scratch. */
+ * plans[i] must outlive the batch; the batch owns its device descriptors and
+ * counters. */
 dd_status dd_batch_create(const dd_plan_t *plans, int nbeams, dd_dtype dtype,
                           dd_batch_t *batch_out);
 void dd_batch_destroy(dd_batch_t batch);
@@ -294,8 +294,7 @@ dd_status dd_sync(dd_plan_t plan, void *stream);
 /* Profiling hook: while set (non-NULL), every execution issued from this
  * thread records start_event just before its de-dispersion kernel and
  * stop_event just after it, on the launch stream (cudaEvent_t handles owned
- * by the caller; the phase-plane pre-pass falls outside the pair).  Pass
- * NULLs to clear. */
+ * by the caller).  Pass NULLs to clear. */
 void dd_profile_events(void *start_event, void *stop_event);
 
 /* Self-test of the kernels' bounded waits: one CTA waits, through the same

@@ -235,7 +235,7 @@ class Plan:
     def execute_noalloc_ptr(self, in_ptr: int, dtype: int, in_pitch: int, nsamp_in: int,
                             out_ptr: int, out_pitch: int, nsamp_out: int, stream: int = 0):
         """dd_execute_noalloc on raw device pointers: for callers that cannot
-        allocate device memory; uses the library's fixed 64 MiB device array."""
+        allocate device memory; uses the library's fixed 1 MiB device array."""
         check(lib.dd_execute_noalloc(self.handle, ctypes.c_void_p(in_ptr), dtype, in_pitch,
                                      nsamp_in, ctypes.c_void_p(out_ptr), out_pitch, nsamp_out,
                                      ctypes.c_void_p(stream)))

@@ -30,8 +30,6 @@ struct BatchBeam {
     float *out = nullptr;
     int64_t out_pitch = 0, nsamp_out = 0;
     bool bound = false;
-    void *scratch = nullptr;
-    size_t scratch_bytes = 0;
     dd::Geometry g;
     int64_t ntiles = 0;
 };
@@ -76,7 +74,7 @@ void drop_graph(dd_batch_s *b) {
     b->prepared = false;
 }
 
-// Geometry, descriptors, scratch and launch shape for the current tiles.
+// Geometry, descriptors and launch shape for the current tiles.
 dd_status prepare(dd_batch_s *b) {
     if (b->prepared)
         return DD_OK;
@@ -101,7 +99,6 @@ dd_status prepare(dd_batch_s *b) {
             return fail(DD_ERR_INVALID, "no tile shape fits every beam of the batch");
         b->tiles_set = true;
     }
-    const int nph = dd::phases(b->dtype);
     const int elem = dd::elem_size(b->dtype);
     int64_t stage_max = 0;
     for (auto &bb : b->beams) {
@@ -110,24 +107,10 @@ dd_status prepare(dd_batch_s *b) {
             return st;
         stage_max = std::max<int64_t>(stage_max, bb.g.stage_bytes);
         bb.ntiles = (int64_t)bb.g.ntile_d * ((bb.nsamp_out + bb.g.t_cta - 1) / bb.g.t_cta);
-        const size_t need = (size_t)dd::scratch_bytes(b->dtype, bb.plan->nchan, bb.in_pitch * elem);
-        if (need > bb.scratch_bytes) {
-            cudaFree(bb.scratch);
-            bb.scratch = nullptr;
-            bb.scratch_bytes = 0;
-            if (need && cudaMalloc(&bb.scratch, need) != cudaSuccess) {
-                cudaGetLastError();
-                return fail(DD_ERR_NOMEM, "batch phase-plane scratch allocation failed");
-            }
-            bb.scratch_bytes = need;
-        }
     }
     const dd::Geometry &g0 = b->beams[0].g;
     // Shared-memory layout sized for the widest beam.
-    auto smem_for = [&](int64_t n) {
-        const int64_t tab = (n * b->tiles.chan_per_stage * g0.dm_cta * 4 + 15) / 16 * 16;
-        return n * stage_max + tab + n * dd::kStageMeta + g0.zero_bytes + 16 * n;
-    };
+    auto smem_for = [&](int64_t n) { return dd::ring_smem(g0, stage_max, (int)n); };
     int nst = 4;
     while (nst > 2 && smem_for(nst) > dd::kMaxSmem)
         --nst;
@@ -151,8 +134,6 @@ dd_status prepare(dd_batch_s *b) {
         dd::BeamArgs &d = desc[k];
         d.in = static_cast<const uint8_t *>(bb.in);
         d.in_pitch_b = bb.in_pitch * elem;
-        d.planes = static_cast<const uint8_t *>(bb.scratch);
-        d.plane_stride = (int64_t)bb.plan->nchan * d.in_pitch_b;
         d.nsamp_in = bb.nsamp_in;
         d.out = bb.out;
         d.out_pitch = bb.out_pitch;
@@ -199,36 +180,18 @@ dd_status prepare(dd_batch_s *b) {
     a.nstages = nst;
     a.stage_bytes = (int)stage_max;
     a.zero_bytes = g0.zero_bytes;
+    a.builders = g0.builders;
     a.one = 1u;
     a.status = b->d_status;
-    (void)nph;
     b->prepared = true;
     return DD_OK;
 }
 
-// Phase planes of every beam, then the persistent de-dispersion launch.
+// The tile counter reset, then the persistent de-dispersion launch.
 dd_status enqueue(dd_batch_s *b, cudaStream_t s, bool count = true) {
     cudaError_t e = cudaMemsetAsync(b->d_counter, 0, sizeof(int), s);
-    int launches = 0;
-    const int elem = dd::elem_size(b->dtype);
-    for (auto &bb : b->beams) {
-        if (e != cudaSuccess)
-            break;
-        const uint8_t *in = static_cast<const uint8_t *>(bb.in);
-        const int64_t pitch_b = bb.in_pitch * elem;
-        const int64_t stride = (int64_t)bb.plan->nchan * pitch_b;
-        if (b->dtype == DD_U8)
-            e = dd::launch_planes_u8(in, pitch_b, bb.plan->nchan, bb.nsamp_in,
-                                     (uint8_t *)bb.scratch, stride, s);
-        else if (b->dtype == DD_F16)
-            e = dd::launch_planes_f16(in, pitch_b, bb.plan->nchan, bb.nsamp_in,
-                                      (uint8_t *)bb.scratch, stride, s);
-        else
-            continue;
-        ++launches;
-    }
     if (e != cudaSuccess)
-        return fail(DD_ERR_CUDA, std::string("batch phase planes: ") + cudaGetErrorString(e));
+        return fail(DD_ERR_CUDA, std::string("batch counter reset: ") + cudaGetErrorString(e));
     const int dthr = b->tiles.dm_per_thread, nw = b->tiles.words_per_thread;
     switch (b->dtype) {
     case DD_U8: e = dd::launch_kernel_u8(b->args, b->grid, b->threads, b->smem, s, dthr, nw); break;
@@ -238,7 +201,7 @@ dd_status enqueue(dd_batch_s *b, cudaStream_t s, bool count = true) {
     if (e != cudaSuccess)
         return fail(DD_ERR_CUDA, std::string("batch kernel launch: ") + cudaGetErrorString(e));
     if (count)
-        dd::count_launch(launches + 1);
+        dd::count_launch(1);
     return DD_OK;
 }
 
@@ -275,8 +238,6 @@ void dd_batch_destroy(dd_batch_t b) {
         cudaSetDevice(b->dev);
     cudaDeviceSynchronize();
     drop_graph(b);
-    for (auto &bb : b->beams)
-        cudaFree(bb.scratch);
     cudaFree(b->d_beams);
     cudaFree(b->d_counter);
     cudaFree(b->d_status);

@@ -48,47 +48,6 @@ struct HostWorkspace {
 
 }  // namespace
 
-namespace dd {
-
-dd_status run_with_plan_scratch(dd_plan_s *p, const Geometry &g, DevTables &dt, const void *in,
-                                dd_dtype dtype, int64_t in_pitch, int64_t nsamp_in, float *out,
-                                int64_t out_pitch, int64_t nsamp_out, void *stream) {
-    const int64_t need = scratch_bytes(dtype, p->nchan, in_pitch * g.elem);
-    cudaStream_t s = static_cast<cudaStream_t>(stream);
-    std::lock_guard<std::mutex> lk(p->mu);  // orders wait/launch/record across threads
-    if (dt.scratch_done == nullptr) {
-        cudaEvent_t ev;
-        if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess)
-            return fail(DD_ERR_CUDA, "event creation failed");
-        dt.scratch_done = ev;
-    }
-    cudaEvent_t done = static_cast<cudaEvent_t>(dt.scratch_done);
-    if ((size_t)need > dt.scratch_bytes) {
-        // cudaFree waits for every use of the old buffer.
-        cudaFree(dt.scratch);
-        dt.scratch = nullptr;
-        dt.scratch_bytes = 0;
-        if (cudaMalloc(&dt.scratch, (size_t)need) != cudaSuccess) {
-            cudaGetLastError();
-            dt.scratch = nullptr;
-            return fail(DD_ERR_NOMEM, "phase-plane scratch allocation failed (" +
-                                          std::to_string(need) + " bytes)");
-        }
-        dt.scratch_bytes = (size_t)need;
-    }
-    if (need > 0 && cudaStreamWaitEvent(s, done, 0) != cudaSuccess)
-        return fail(DD_ERR_CUDA, "stream wait on scratch event failed");
-    dd_status st = launch_dedisperse(p, g, dt, in, dtype, in_pitch, nsamp_in, out, out_pitch,
-                                     nsamp_out, dt.scratch, stream);
-    if (st != DD_OK)
-        return st;
-    if (need > 0 && cudaEventRecord(done, s) != cudaSuccess)
-        return fail(DD_ERR_CUDA, "scratch event record failed");
-    return DD_OK;
-}
-
-}  // namespace dd
-
 extern "C" dd_status dd_execute(dd_plan_t p, const void *in, dd_dtype dtype, int64_t in_pitch,
                                 int64_t nsamp_in, float *out, int64_t out_pitch,
                                 int64_t nsamp_out, void *stream) {
@@ -107,8 +66,8 @@ extern "C" dd_status dd_execute(dd_plan_t p, const void *in, dd_dtype dtype, int
     dd::DevTables *dt = nullptr;
     if ((st = dd::device_tables(p, &dt)) != DD_OK)
         return st;
-    return dd::run_with_plan_scratch(p, g, *dt, in, dtype, in_pitch, nsamp_in, out, out_pitch,
-                                     nsamp_out, stream);
+    return dd::launch_dedisperse(p, g, *dt, in, dtype, in_pitch, nsamp_in, out, out_pitch,
+                                 nsamp_out, stream);
 }
 
 extern "C" dd_status dd_sync(dd_plan_t p, void *stream) {
@@ -230,7 +189,7 @@ extern "C" dd_status dd_execute_host(dd_plan_t p, const void *in_host, dd_dtype 
             e = cudaEventRecord(ws.landed[i], s);
         if (e != cudaSuccess)
             return fail(DD_ERR_CUDA, std::string("input copy: ") + cudaGetErrorString(e));
-        st = dd::run_with_plan_scratch(p, g, *dt, din, dtype, dpitch_in / elem, nb + S,
+        st = dd::launch_dedisperse(p, g, *dt, din, dtype, dpitch_in / elem, nb + S,
                                        ws.out[i], dpitch_out, nb, s);
         if (st != DD_OK)
             return st;
@@ -300,11 +259,11 @@ extern "C" dd_status dd_autotune(dd_plan_t p, const void *in, dd_dtype dtype, in
         dd::Geometry g;
         float ms = -1.0f;
         if (dd::make_geometry(p, dtype, cand, &g) == DD_OK) {
-            st = dd::run_with_plan_scratch(p, g, *dt, in, dtype, in_pitch, nsamp_in, out,
+            st = dd::launch_dedisperse(p, g, *dt, in, dtype, in_pitch, nsamp_in, out,
                                            out_pitch, nsamp_out, s);  // warm-up
             for (int r = 0; r < reps && st == DD_OK; ++r) {
                 cudaEventRecord(e0, s);
-                st = dd::run_with_plan_scratch(p, g, *dt, in, dtype, in_pitch, nsamp_in, out,
+                st = dd::launch_dedisperse(p, g, *dt, in, dtype, in_pitch, nsamp_in, out,
                                                out_pitch, nsamp_out, s);
                 cudaEventRecord(e1, s);
                 if (cudaEventSynchronize(e1) != cudaSuccess) {

@@ -27,10 +27,16 @@ constexpr int kFloatBlock = 64;
 constexpr int kMaxSmem = 232448;  // 227 KB dynamic shared memory per CTA
 constexpr int kMaxDmPerCta = 64;   // DMs per CTA (offset-table columns, DM padding)
 constexpr int kStageMeta = 32;     // bytes of a stage record in shared memory
-// Consumer warps per CTA (plus one producer warp), from the registers a
-// thread needs: accumulators 2*DT*NW (uint8) + two load buffers 4*NW + ~24.
-// 13 warps leave 128 registers a thread (at most 4 warps per SM
-// sub-partition), 17 leave 96, 21 leave 85, 25 leave 73.
+// Builder warps (8/16-bit input) derive the byte phases 1.. of every staged
+// row from phase 0 in shared memory; the producer records the bytes staged
+// per row (kRowInfoBytes per stage: one word per row, at most 64 rows).
+constexpr int kMaxBuilders = 2;
+constexpr int kRowInfoBytes = 256;
+// Consumer warps per CTA (plus one producer warp and, for 8/16-bit input, the
+// builder warps), from the registers a thread needs: accumulators 2*DT*NW
+// (uint8) + two load buffers 4*NW + ~24.  A CTA of at most 16 warps leaves
+// 128 registers a thread (at most 4 warps per SM sub-partition), at most 20
+// leave 96, at most 24 leave 80, at most 28 leave 72.
 #ifdef __CUDACC__
 #define DD_HD __host__ __device__
 #else
@@ -52,11 +58,6 @@ struct DevTables {
     int *perm = nullptr;         // [ndm_pad]: output row of sorted DM k, -1 for padding
     int *status = nullptr;       // device status word
     int ndm_pad = 0;
-    // Phase-plane scratch of dd_execute (grown on demand).  Uses on different
-    // streams are ordered by scratch_done: each use waits for the previous one.
-    void *scratch = nullptr;
-    size_t scratch_bytes = 0;
-    void *scratch_done = nullptr;  // cudaEvent_t
 };
 
 // Launch geometry derived from a tile shape and the plan's tables.
@@ -71,7 +72,8 @@ struct Geometry {
     int nstages = 0;      // shared-memory stages in the copy ring
     int zero_bytes = 0;   // zero row read by padding channels
     int smem = 0;         // dynamic shared memory per CTA
-    int threads = 0;      // consumer warps + one producer warp
+    int builders = 0;     // phase-builder warps (0 for FP32)
+    int threads = 0;      // consumer warps + one producer warp + builder warps
 };
 
 }  // namespace dd
@@ -96,6 +98,12 @@ namespace dd {
 // Thread-local error message; returns st for chaining.
 dd_status fail(dd_status st, const std::string &msg);
 
+// Dynamic shared memory of a ring of n stages of stage_bytes each for a
+// geometry: the stages, the offset table, the stage records, the per-row
+// byte counts (with phases to build), the zero row and three mbarriers per
+// stage, in the order the kernel lays them out.
+int64_t ring_smem(const Geometry &g, int64_t stage_bytes, int n);
+
 // Preferred tile shape for a dtype.
 dd_tiles default_tiles(dd_dtype t);
 
@@ -114,20 +122,10 @@ dd_status plan_geometry(dd_plan_s *p, dd_dtype t, Geometry *g);
 // Device tables for the current device, uploaded on first use.
 dd_status device_tables(dd_plan_s *p, DevTables **out);
 
-// Bytes of phase-plane scratch for one input (0 for FP32).
-int64_t scratch_bytes(dd_dtype dtype, int nchan, int64_t in_pitch_b);
-
-// Launch the phase-plane pre-pass (8/16-bit input) and the de-dispersion
-// kernel (dd_kernel.cu) on stream, with caller-provided scratch.
+// Launch the de-dispersion kernel (dd_kernel_*.cu) for one beam on stream.
 dd_status launch_dedisperse(dd_plan_s *p, const Geometry &g, const DevTables &dt,
                             const void *in, dd_dtype dtype, int64_t in_pitch, int64_t nsamp_in,
-                            float *out, int64_t out_pitch, int64_t nsamp_out, void *scratch,
-                            void *stream);
-
-// launch_dedisperse with the plan's own per-device scratch (dd_exec.cpp).
-dd_status run_with_plan_scratch(dd_plan_s *p, const Geometry &g, DevTables &dt, const void *in,
-                                dd_dtype dtype, int64_t in_pitch, int64_t nsamp_in, float *out,
-                                int64_t out_pitch, int64_t nsamp_out, void *stream);
+                            float *out, int64_t out_pitch, int64_t nsamp_out, void *stream);
 
 void count_launch(int n = 1);
 

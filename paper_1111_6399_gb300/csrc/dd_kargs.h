@@ -11,8 +11,6 @@ namespace dd {
 // One beam: its buffers, plan tables and launch geometry.
 struct BeamArgs {
     const uint8_t *in;
-    const uint8_t *planes;  // byte-phase planes 1..NPH-1 (NULL for FP32)
-    int64_t plane_stride;   // bytes between planes
     int64_t in_pitch_b;     // bytes between channel rows
     int64_t nsamp_in;       // valid samples per row
     float *out;
@@ -43,6 +41,7 @@ struct KArgs {
     int stage_bytes;        // capacity of one ring stage
     int zero_bytes;         // bytes of the zero row (padding channels)
     uint32_t one;           // the constant 1, opaque to the compiler
+    int builders;           // phase-builder warps (8/16-bit input; 0 for FP32)
     int *status;
 };
 
@@ -53,11 +52,6 @@ cudaError_t launch_kernel_f16(const KArgs &a, unsigned grid, int threads, int sm
                               cudaStream_t s, int dthr, int nw);
 cudaError_t launch_kernel_f32(const KArgs &a, unsigned grid, int threads, int smem,
                               cudaStream_t s, int dthr, int nw);
-// Byte-phase planes of an 8- or 16-bit input (pre-pass).
-cudaError_t launch_planes_u8(const uint8_t *in, int64_t pitch_b, int nchan, int64_t nsamp_in,
-                             uint8_t *planes, int64_t plane_stride, cudaStream_t s);
-cudaError_t launch_planes_f16(const uint8_t *in, int64_t pitch_b, int nchan, int64_t nsamp_in,
-                              uint8_t *planes, int64_t plane_stride, cudaStream_t s);
 
 // Shared-memory bytes of the per-stage metadata record.
 constexpr int kStageMetaBytes = 32;

@@ -13,13 +13,15 @@
 //    (DM,t) (Fig. 2).
 //  * Data next to the SMs.  A producer warp stages each channel's window
 //    [t0 + s(c,dm_min), t0 + T + s(c,dm_max)) with TMA bulk copies (no
-//    multicast) into a ring of shared-memory stages handed over through
-//    full/empty mbarriers, so copies run ahead of the arithmetic and no
-//    CTA-wide barrier sits in the loop.  Shifts are arbitrary in bytes while
-//    shared-memory words are 4-byte aligned, so for 8/16-bit data the window
-//    is staged once per byte phase (1..3 or 2 bytes later), fetched from phase
-//    planes that a pre-pass writes to global scratch; every shifted read is
-//    then an aligned, conflict-free LDS.32.
+//    multicast) into a ring of shared-memory stages.  Shifts are arbitrary in
+//    bytes while shared-memory words are 4-byte aligned, so for 8/16-bit data
+//    every staged row is kept once per byte phase (advanced by 1..3 bytes, or
+//    by one FP16 sample): the copy brings phase 0 and builder warps derive the
+//    other phases from it in shared memory with byte permutes, so HBM and L2
+//    carry each window once.  Every shifted read is then an aligned,
+//    conflict-free LDS.32.  Stages pass producer -> builders -> consumers ->
+//    producer through raw/full/empty mbarriers, so copies and phase building
+//    run ahead of the arithmetic and no CTA-wide barrier sits in the loop.
 //  * Shift arithmetic.  The producer computes, per staged channel and DM of
 //    the tile, the shared-memory offset of the shifted window (one FP32
 //    multiply and one truncation) into a small table; consumers fetch the
@@ -35,10 +37,10 @@
 //
 // Work distribution.  The producer decides which tile the CTA works on and
 // tags every stage with it (beam, DM tile, first sample, stage number); the
-// consumers follow that stream until a terminating stage.  A single-beam
-// launch gives each CTA one tile (blockIdx.x); a batch launch is persistent
-// (one CTA per SM) and the producer claims tiles of many beams, largest
-// first, from an atomic counter.
+// builders and consumers follow that stream until a terminating stage.  A
+// single-beam launch gives each CTA one tile (blockIdx.x); a batch launch is
+// persistent (one CTA per SM) and the producer claims tiles of many beams,
+// largest first, from an atomic counter.
 //
 // Every mbarrier wait is bounded by the global timer; a wait that runs out
 // records a timeout in the status word and the thread leaves (the producer
@@ -200,40 +202,6 @@ __device__ __forceinline__ void store4(float *row, int64_t t, int64_t n, float4 
     }
 }
 
-// ---------------------------------------------------------------------------
-// Pre-pass: byte-phase planes.  Plane p (1 <= p < NPH) holds every input row
-// advanced by p bytes (uint8) or by one sample (FP16): plane byte j of row c
-// is input byte j + p*ELEM of row c.
-// ---------------------------------------------------------------------------
-template <int ELEM>
-__global__ void __launch_bounds__(256) phase_planes_kernel(const uint8_t *__restrict__ in,
-                                                           int64_t pitch_b, int nchan,
-                                                           int64_t groups_per_row,
-                                                           uint8_t *__restrict__ planes,
-                                                           int64_t plane_stride) {
-    constexpr int NPH = 4 / ELEM;
-    const int64_t total = groups_per_row * nchan;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t c = i / groups_per_row;
-        const int64_t g = i - c * groups_per_row;
-        const uint8_t *row = in + c * pitch_b + 16 * g;
-        const uint4 v = *reinterpret_cast<const uint4 *>(row);
-        const uint32_t nx =
-            (16 * g + 16 < pitch_b) ? *reinterpret_cast<const uint32_t *>(row + 16) : 0u;
-#pragma unroll
-        for (int p = 1; p < NPH; ++p) {
-            const uint32_t sel = (ELEM == 1) ? (0x3210u + 0x1111u * (uint32_t)p) : 0x5432u;
-            uint4 o;
-            o.x = prmt(v.x, v.y, sel);
-            o.y = prmt(v.y, v.z, sel);
-            o.z = prmt(v.z, v.w, sel);
-            o.w = prmt(v.w, nx, sel);
-            *reinterpret_cast<uint4 *>(planes + (p - 1) * plane_stride + c * pitch_b + 16 * g) = o;
-        }
-    }
-}
-
 __device__ __forceinline__ const BeamArgs &beam_at(const KArgs &a, int i) {
     return a.beams ? a.beams[i] : a.beam0;
 }
@@ -256,12 +224,13 @@ __device__ __forceinline__ int beam_of_tile(const KArgs &a, int64_t tile) {
 // ---------------------------------------------------------------------------
 // The de-dispersion kernel.  ELEM = bytes per sample (1, 2, 4); DT = DMs per
 // consumer thread; NW = 4-byte words per DM per consumer thread (4 or 8).
-// Warps 0..ncw-1 consume, warp ncw produces.
+// Warps 0..ncw-1 consume, warp ncw produces, warps ncw+1.. build phases.
 // ---------------------------------------------------------------------------
 template <int ELEM, int DT, int NW>
-__global__ void __launch_bounds__(32 * (max_consumer_warps(DT, NW) + 1), 1)
+__global__ void __launch_bounds__(32 * (max_consumer_warps(DT, NW) + 1 + (ELEM < 4 ? kMaxBuilders : 0)), 1)
     dedisperse_kernel(const __grid_constant__ KArgs a) {
     constexpr int NPH = 4 / ELEM;            // phase copies per row
+    constexpr bool BUILD = NPH > 1;          // phases 1.. are built in shared memory
     constexpr int SPW = 4 / ELEM;            // samples per 4-byte word
     constexpr int SPAN = 32 * NW * SPW;      // samples per warp
     constexpr int FLUSH = (ELEM == 1) ? kSwarChannels : kFloatBlock;
@@ -281,18 +250,27 @@ __global__ void __launch_bounds__(32 * (max_consumer_warps(DT, NW) + 1), 1)
     int *atab = reinterpret_cast<int *>(smem + nst * stage_bytes);
     StageMeta *meta = reinterpret_cast<StageMeta *>(
         smem + nst * stage_bytes + ((nst * tab_stride * 4 + 15) & ~15));
-    uint8_t *zero = reinterpret_cast<uint8_t *>(meta) + nst * kStageMetaBytes;
+    // Bytes staged for each row of each stage (phase 0), for the builders.
+    uint32_t *rowb = reinterpret_cast<uint32_t *>(reinterpret_cast<uint8_t *>(meta) +
+                                                  nst * kStageMetaBytes);
+    uint8_t *zero = reinterpret_cast<uint8_t *>(rowb) + (BUILD ? nst * kRowInfoBytes : 0);
     uint64_t *mbar = reinterpret_cast<uint64_t *>(zero + a.zero_bytes);
     const uint32_t full0 = smem_addr(&mbar[0]);
     const uint32_t empty0 = smem_addr(&mbar[nst]);
+    const uint32_t raw0 = smem_addr(&mbar[2 * nst]);
+    // The producer hands a stage to the builders (raw) or, without phases to
+    // build, straight to the consumers (full).
+    const uint32_t hand0 = BUILD ? raw0 : full0;
+    const int nbw = BUILD ? a.builders : 0;
     const int zero_off = (int)(zero - smem);
 
     for (int i = tid; i < a.zero_bytes / 16; i += blockDim.x)
         reinterpret_cast<uint4 *>(zero)[i] = make_uint4(0, 0, 0, 0);
     if (tid == 0) {
         for (int b = 0; b < nst; ++b) {
-            mbar_init(full0 + 8 * b, 1);
+            mbar_init(full0 + 8 * b, BUILD ? nbw : 1);
             mbar_init(empty0 + 8 * b, ncw);
+            mbar_init(raw0 + 8 * b, 1);
         }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -396,25 +374,22 @@ __global__ void __launch_bounds__(32 * (max_consumer_warps(DT, NW) + 1), 1)
                 // arrival, the copies are issued, and the offset table is written
                 // while they are in flight; the arrival then releases the stage
                 // (the phase completes once it and every byte are in).
-                uint32_t total = (my_bytes[0] + my_bytes[1]) * NPH;
+                uint32_t total = my_bytes[0] + my_bytes[1];
 #pragma unroll
                 for (int o = 16; o > 0; o >>= 1)
                     total += __shfl_xor_sync(0xffffffffu, total, o);
                 if (lane == 0)
-                    mbar_expect_tx(full0 + 8 * b, total);
+                    mbar_expect_tx(hand0 + 8 * b, total);
                 __syncwarp();
                 for (int h = 0; h < 2; ++h) {
                     const int r = lane + 32 * h;
+                    if (BUILD && r < cstage)
+                        rowb[b * (kRowInfoBytes / 4) + r] = my_bytes[h];
                     if (r >= cstage || my_bytes[h] == 0)
                         continue;
                     const int c = st * cstage + r;
                     const int64_t off = (int64_t)c * B.in_pitch_b + my_first[h] * ELEM;
-                    const uint32_t dst = smem_addr(buf + r * row_bytes);
-                    bulk_g2s(dst, B.in + off, my_bytes[h], full0 + 8 * b);
-#pragma unroll
-                    for (int p = 1; p < NPH; ++p)
-                        bulk_g2s(dst + p * wp, B.planes + (p - 1) * B.plane_stride + off,
-                                 my_bytes[h], full0 + 8 * b);
+                    bulk_g2s(smem_addr(buf + r * row_bytes), B.in + off, my_bytes[h], hand0 + 8 * b);
                 }
                 // Offset table: row r, DM k -> smem offset of the shifted window.
                 for (int r = 0; r < cstage; ++r) {
@@ -433,7 +408,7 @@ __global__ void __launch_bounds__(32 * (max_consumer_warps(DT, NW) + 1), 1)
                 }
                 __syncwarp();
                 if (lane == 0)
-                    mbar_arrive(full0 + 8 * b);
+                    mbar_arrive(hand0 + 8 * b);
             }
             if (!ok)
                 break;
@@ -456,7 +431,7 @@ __global__ void __launch_bounds__(32 * (max_consumer_warps(DT, NW) + 1), 1)
                 }
                 __syncwarp();
                 if (lane == 0)
-                    mbar_arrive(full0 + 8 * b);
+                    mbar_arrive(hand0 + 8 * b);
             }
         }
         if (!ok)
@@ -465,12 +440,80 @@ __global__ void __launch_bounds__(32 * (max_consumer_warps(DT, NW) + 1), 1)
         // normally, been released by the consumers); bounded.
         for (int64_t q = (real > nst ? real - nst : 0); q < real; ++q) {
             const int b = (int)(q % nst);
-            if (!mbar_wait(ok ? empty0 + 8 * b : full0 + 8 * b, (uint32_t)((q / nst) & 1))) {
+            if (!mbar_wait(ok ? empty0 + 8 * b : hand0 + 8 * b, (uint32_t)((q / nst) & 1))) {
                 record(a.status, kDevTimeout);
                 break;
             }
         }
         return;
+    }
+
+    if (BUILD && warp > ncw) {
+        // ------------------------------ builders ------------------------------
+        // Phase p of a staged row is phase 0 advanced by p bytes (uint8) or by
+        // one sample (FP16): word i of phase p takes bytes i*4+p .. i*4+p+3 of
+        // phase 0.  Builder w handles rows w, w + nbw, ..., two rows at a time
+        // (two independent chains of loads in flight); lane l takes 16-byte
+        // chunk j = j0 + l.  Bytes past the copied window only reach samples
+        // outside the tile or past nsamp_out.
+        const int bw = warp - ncw - 1;
+        for (int64_t g = 0;; ++g) {
+            const int b = (int)(g % nst);
+            if (!mbar_wait(raw0 + 8 * b, (uint32_t)((g / nst) & 1))) {
+                record(a.status, kDevTimeout);
+                return;
+            }
+            const int mbeam = meta[b].beam;
+            const bool stop = mbeam < 0;
+            if (!stop) {
+                const int row_bytes = NPH * beam_at(a, mbeam).wp;
+                const int wp = row_bytes / NPH;
+                uint8_t *buf = smem + b * stage_bytes;
+                const uint32_t *nb = rowb + b * (kRowInfoBytes / 4);
+                for (int r0 = bw; r0 < cstage; r0 += 2 * nbw) {
+                    const int r1 = r0 + nbw;
+                    const int n0 = (int)(nb[r0] >> 4);
+                    const int n1 = r1 < cstage ? (int)(nb[r1] >> 4) : 0;
+                    uint8_t *row0 = buf + r0 * row_bytes;
+                    uint8_t *row1 = buf + min(r1, cstage - 1) * row_bytes;
+                    const int nmax = max(n0, n1);
+                    for (int j0 = 0; j0 < nmax; j0 += 32) {
+                        const int j = j0 + lane;
+                        // Both rows' loads are issued before any store.  The
+                        // word after a chunk lies inside phase 0 of its row
+                        // (the copied window ends at least 16 bytes before
+                        // phase 1).
+                        uint4 v0 = make_uint4(0, 0, 0, 0), v1 = v0;
+                        uint32_t x0 = 0, x1 = 0;
+                        if (j < n0) {
+                            v0 = *reinterpret_cast<const uint4 *>(row0 + 16 * j);
+                            x0 = *reinterpret_cast<const uint32_t *>(row0 + 16 * j + 16);
+                        }
+                        if (j < n1) {
+                            v1 = *reinterpret_cast<const uint4 *>(row1 + 16 * j);
+                            x1 = *reinterpret_cast<const uint32_t *>(row1 + 16 * j + 16);
+                        }
+#pragma unroll
+                        for (int p = 1; p < NPH; ++p) {
+                            const uint32_t sp = (ELEM == 1) ? 0x3210u + 0x1111u * (uint32_t)p : 0x5432u;
+                            if (j < n0)
+                                *reinterpret_cast<uint4 *>(row0 + p * wp + 16 * j) =
+                                    make_uint4(prmt(v0.x, v0.y, sp), prmt(v0.y, v0.z, sp),
+                                               prmt(v0.z, v0.w, sp), prmt(v0.w, x0, sp));
+                            if (j < n1)
+                                *reinterpret_cast<uint4 *>(row1 + p * wp + 16 * j) =
+                                    make_uint4(prmt(v1.x, v1.y, sp), prmt(v1.y, v1.z, sp),
+                                               prmt(v1.z, v1.w, sp), prmt(v1.w, x1, sp));
+                        }
+                    }
+                }
+            }
+            __syncwarp();
+            if (lane == 0)
+                mbar_arrive(full0 + 8 * b);
+            if (stop)
+                return;
+        }
     }
 
     // ------------------------------- consumers --------------------------------
@@ -734,17 +777,6 @@ cudaError_t launch_elem(const KArgs &a, unsigned grid, int threads, int smem, cu
         }
     }
     return cudaErrorInvalidValue;
-}
-
-template <int ELEM>
-cudaError_t launch_planes_elem(const uint8_t *in, int64_t pitch_b, int nchan, int64_t nsamp_in,
-                               uint8_t *planes, int64_t plane_stride, cudaStream_t s) {
-    const int64_t groups = (nsamp_in * ELEM + 15) / 16;
-    const int64_t total = groups * nchan;
-    const int64_t blocks = std::min<int64_t>((total + 255) / 256, 152 * 16);
-    phase_planes_kernel<ELEM><<<(unsigned)blocks, 256, 0, s>>>(in, pitch_b, nchan, groups, planes,
-                                                               plane_stride);
-    return cudaGetLastError();
 }
 
 }  // namespace

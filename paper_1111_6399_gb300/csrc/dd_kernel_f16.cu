@@ -8,9 +8,4 @@ cudaError_t launch_kernel_f16(const KArgs &a, unsigned grid, int threads, int sm
     return launch_elem<2>(a, grid, threads, smem, s, dthr, nw);
 }
 
-cudaError_t launch_planes_f16(const uint8_t *in, int64_t pitch_b, int nchan, int64_t nsamp_in,
-                             uint8_t *planes, int64_t plane_stride, cudaStream_t s) {
-    return launch_planes_elem<2>(in, pitch_b, nchan, nsamp_in, planes, plane_stride, s);
-}
-
 }  // namespace dd

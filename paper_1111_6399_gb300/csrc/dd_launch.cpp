@@ -1,5 +1,5 @@
-// Host side of a de-dispersion launch: kernel arguments, the phase-plane
-// pre-pass, the per-dtype kernel dispatch and the profiling-event hook.
+// Host side of a de-dispersion launch: kernel arguments, the per-dtype kernel
+// dispatch and the profiling-event hook.
 #include <cuda_runtime_api.h>
 
 #include <string>
@@ -15,21 +15,15 @@ thread_local cudaEvent_t g_prof_stop = nullptr;
 
 }  // namespace
 
-int64_t scratch_bytes(dd_dtype dtype, int nchan, int64_t in_pitch_b) {
-    return (int64_t)(phases(dtype) - 1) * nchan * in_pitch_b;
-}
-
 dd_status launch_dedisperse(dd_plan_s *p, const Geometry &g, const DevTables &dt, const void *in,
                             dd_dtype dtype, int64_t in_pitch, int64_t nsamp_in, float *out,
-                            int64_t out_pitch, int64_t nsamp_out, void *scratch, void *stream) {
+                            int64_t out_pitch, int64_t nsamp_out, void *stream) {
     if (nsamp_out == 0)
         return DD_OK;
     KArgs a{};
     BeamArgs &b = a.beam0;
     b.in = static_cast<const uint8_t *>(in);
     b.in_pitch_b = in_pitch * g.elem;
-    b.planes = static_cast<const uint8_t *>(scratch);
-    b.plane_stride = (int64_t)p->nchan * b.in_pitch_b;
     b.nsamp_in = nsamp_in;
     b.out = out;
     b.out_pitch = out_pitch;
@@ -50,6 +44,7 @@ dd_status launch_dedisperse(dd_plan_s *p, const Geometry &g, const DevTables &dt
     a.nstages = g.nstages;
     a.stage_bytes = g.stage_bytes;
     a.zero_bytes = g.zero_bytes;
+    a.builders = g.builders;
     a.one = 1u;
     a.status = dt.status;
     const int64_t ntile_t = (nsamp_out + g.t_cta - 1) / g.t_cta;
@@ -57,22 +52,8 @@ dd_status launch_dedisperse(dd_plan_s *p, const Geometry &g, const DevTables &dt
     if (ntiles > 0x7fffffffLL)
         return fail(DD_ERR_INVALID, "too many tiles for one launch");
     a.total_tiles = ntiles;
-    if (g.nph > 1 && scratch == nullptr)
-        return fail(DD_ERR_INVALID, "phase-plane scratch missing");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     cudaError_t e = cudaSuccess;
-    int launches = 1;
-    if (dtype == DD_U8) {
-        e = launch_planes_u8(b.in, b.in_pitch_b, p->nchan, nsamp_in, (uint8_t *)scratch,
-                             b.plane_stride, s);
-        ++launches;
-    } else if (dtype == DD_F16) {
-        e = launch_planes_f16(b.in, b.in_pitch_b, p->nchan, nsamp_in, (uint8_t *)scratch,
-                              b.plane_stride, s);
-        ++launches;
-    }
-    if (e != cudaSuccess)
-        return fail(DD_ERR_CUDA, std::string("phase-plane launch failed: ") + cudaGetErrorString(e));
     if (g_prof_start)
         cudaEventRecord(g_prof_start, s);
     const unsigned grid = (unsigned)ntiles;
@@ -86,7 +67,7 @@ dd_status launch_dedisperse(dd_plan_s *p, const Geometry &g, const DevTables &dt
         return fail(DD_ERR_CUDA, std::string("kernel launch failed: ") + cudaGetErrorString(e));
     if (g_prof_stop)
         cudaEventRecord(g_prof_stop, s);
-    count_launch(launches);
+    count_launch(1);
     return DD_OK;
 }
 

@@ -5,10 +5,9 @@
 // allocator or a memory-pool callback, real-time threads that must not take
 // the driver's allocation locks, and hosts that forbid the library from
 // owning device memory.  For them this entry point keeps everything the
-// kernels need beyond the caller's input and output -- the plan's device
-// tables, the status word and the byte-phase planes -- in one file-scope
-// device array of fixed size, and writes it with plain copies and a memset on
-// the caller's stream.
+// kernel needs beyond the caller's input and output -- the plan's device
+// tables and the status word -- in one file-scope device array of fixed
+// size, and writes it with plain copies and a memset on the caller's stream.
 //
 // The array is shared by every call in the process: a call overwrites what
 // the previous one left there, so calls whose GPU work overlaps (on
@@ -26,7 +25,7 @@
 
 namespace {
 
-constexpr size_t kNoAllocBytes = (size_t)64 << 20;  // 64 MiB
+constexpr size_t kNoAllocBytes = (size_t)1 << 20;  // 1 MiB
 
 // Device-side scratch of dd_execute_noalloc.  In host code this name is a
 // host-side stand-in, not a device address: the address handed to kernels
@@ -87,14 +86,12 @@ extern "C" dd_status dd_execute_noalloc(dd_plan_t p, const void *in, dd_dtype dt
     const size_t off_dmshift = 256;
     const size_t off_dm = off_dmshift + align256(sizeof(float) * (size_t)p->nchan);
     const size_t off_perm = off_dm + align256(sizeof(float) * (size_t)ndm_pad);
-    const size_t off_planes = off_perm + align256(sizeof(int) * (size_t)ndm_pad);
-    const size_t planes = (size_t)dd::scratch_bytes(dtype, p->nchan, in_pitch * elem);
-    const size_t need = off_planes + planes;
+    const size_t need = off_perm + align256(sizeof(int) * (size_t)ndm_pad);
     if (need > kNoAllocBytes)
         return fail(DD_ERR_INVALID,
-                    "input too large for dd_execute_noalloc: it needs " + std::to_string(need) +
-                        " bytes of its fixed " + std::to_string(kNoAllocBytes) +
-                        "-byte scratch; use dd_execute");
+                    "plan too large for dd_execute_noalloc: its tables need " +
+                        std::to_string(need) + " bytes of the fixed " +
+                        std::to_string(kNoAllocBytes) + "-byte array; use dd_execute");
 
     dd::Geometry g;
     dd_status st = dd::plan_geometry(p, dtype, &g);
@@ -134,5 +131,5 @@ extern "C" dd_status dd_execute_noalloc(dd_plan_t p, const void *in, dd_dtype dt
     dt.status = reinterpret_cast<int *>(b + off_status);
     dt.ndm_pad = ndm_pad;
     return dd::launch_dedisperse(p, g, dt, in, dtype, in_pitch, nsamp_in, out, out_pitch,
-                                 nsamp_out, planes ? b + off_planes : nullptr, stream);
+                                 nsamp_out, stream);
 }

@@ -74,6 +74,12 @@ std::vector<dd_tiles> auto_tiles(dd_dtype t) {
     return out;
 }
 
+int64_t ring_smem(const Geometry &g, int64_t stage_bytes, int n) {
+    const int64_t table = ((int64_t)n * g.tiles.chan_per_stage * g.dm_cta * 4 + 15) / 16 * 16;
+    const int64_t rowinfo = g.nph > 1 ? kRowInfoBytes : 0;
+    return n * stage_bytes + table + n * (kStageMeta + rowinfo) + g.zero_bytes + 24 * (int64_t)n;
+}
+
 dd_status make_geometry(dd_plan_s *p, dd_dtype t, const dd_tiles &tl, Geometry *g) {
     if (!valid_dtype(t))
         return fail(DD_ERR_INVALID, "unknown dtype");
@@ -127,13 +133,12 @@ dd_status make_geometry(dd_plan_s *p, dd_dtype t, const dd_tiles &tl, Geometry *
     const int64_t wp = widest + 16;
     const int64_t zero_bytes = ((int64_t)r.elem * r.t_cta + 16 + 15) / 16 * 16;
     // Per stage: the staged rows (every byte phase), the producer's offset
-    // table (one int per staged row and DM of the CTA) and a stage record;
-    // then the zero row and two mbarriers per stage.
+    // table (one int per staged row and DM of the CTA), a stage record and,
+    // with phases to build, the bytes staged per row; then the zero row and
+    // three mbarriers per stage.
     const int64_t stage_bytes = (int64_t)tl.chan_per_stage * r.nph * wp;
-    auto smem_for = [&](int64_t n) {
-        const int64_t table = (n * tl.chan_per_stage * r.dm_cta * 4 + 15) / 16 * 16;
-        return n * stage_bytes + table + n * kStageMeta + zero_bytes + 16 * n;
-    };
+    r.zero_bytes = (int)zero_bytes;
+    auto smem_for = [&](int64_t n) { return ring_smem(r, stage_bytes, (int)n); };
     int nst = 4;
     while (nst > 2 && smem_for(nst) > kMaxSmem)
         --nst;
@@ -147,7 +152,11 @@ dd_status make_geometry(dd_plan_s *p, dd_dtype t, const dd_tiles &tl, Geometry *
     r.nstages = nst;
     r.zero_bytes = (int)zero_bytes;
     r.smem = (int)smem;
-    r.threads += 32;  // producer warp
+    // Two builder warps: with one, building a stage (about 3 shared-memory
+    // ops per staged byte, queued behind the consumers' loads) can take
+    // longer than consuming it.
+    r.builders = r.nph > 1 ? kMaxBuilders : 0;
+    r.threads += 32 * (1 + r.builders);  // producer warp, builder warps
     *g = r;
     return DD_OK;
 }
@@ -298,11 +307,6 @@ void dd_plan_destroy(dd_plan_t p) {
     cudaGetDevice(&cur);
     for (auto &kv : p->dev) {
         cudaSetDevice(kv.first);
-        if (kv.second.scratch_done)
-            cudaEventSynchronize((cudaEvent_t)kv.second.scratch_done);
-        cudaFree(kv.second.scratch);
-        if (kv.second.scratch_done)
-            cudaEventDestroy((cudaEvent_t)kv.second.scratch_done);
         cudaFree(kv.second.dmshift);
         cudaFree(kv.second.dm_sorted);
         cudaFree(kv.second.perm);

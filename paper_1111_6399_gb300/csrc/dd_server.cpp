@@ -8,8 +8,8 @@
 // tail.  A worker thread takes every queued block whose beam is ready (the
 // previous block of that beam has been launched, so its tail update is
 // ordered before this block's assembly by an event) up to the free slots,
-// and launches them together: the phase-plane pre-pass of each slot, then one
-// persistent de-dispersion launch over all their tiles, then the copies of
+// and launches them together: one persistent de-dispersion launch over all
+// their tiles, then the copies of
 // the outputs into the callers' buffers.  Batches alternate between two
 // streams, so the copies of one batch overlap the kernel of the other.  A
 // completion thread watches per-block events, records submit-to-result
@@ -66,7 +66,6 @@ struct SrvReq {
 
 struct Slot {
     void *in = nullptr;
-    void *planes = nullptr;
     float *out = nullptr;
     bool busy = false;
 };
@@ -86,7 +85,7 @@ struct dd_server_s {
     size_t budget = 0;
     int max_inflight = 0;
     dd_dtype dtype = DD_U8;
-    int elem = 1, nph = 4;
+    int elem = 1;
     std::vector<SrvBeam> beams;
     bool started = false;
     int dev = 0;
@@ -94,14 +93,14 @@ struct dd_server_s {
     std::vector<Slot> slots;
     int64_t in_pitch = 0;      // slot input pitch, elements
     int64_t out_pitch = 0;     // slot output pitch, floats
-    size_t in_bytes = 0, planes_bytes = 0, out_bytes = 0;
+    size_t in_bytes = 0, out_bytes = 0;
     std::vector<void *> staging;
     std::vector<bool> staging_busy;
     size_t staging_bytes = 0;
     int64_t device_bytes = 0;
     // launch shape
     dd_tiles tiles{};
-    int threads = 0, smem = 0, nst = 2, stage_max = 0, zero_bytes = 0, nsm = 1;
+    int threads = 0, smem = 0, nst = 2, stage_max = 0, zero_bytes = 0, builders = 0, nsm = 1;
     int *d_status = nullptr;
     Lane lanes[2];
     int next_lane = 0;
@@ -126,7 +125,6 @@ size_t round16(size_t x) { return (x + 15) & ~(size_t)15; }
 void free_all(dd_server_s *v) {
     for (auto &s : v->slots) {
         cudaFree(s.in);
-        cudaFree(s.planes);
         cudaFree(s.out);
     }
     v->slots.clear();
@@ -189,10 +187,7 @@ dd_status start(dd_server_s *v) {
         tails += (int64_t)b.plan->nchan * b.tail_pitch * v->elem;
     }
     const dd::Geometry &g0 = v->beams[0].g;
-    auto smem_for = [&](int64_t n) {
-        const int64_t tab = (n * v->tiles.chan_per_stage * g0.dm_cta * 4 + 15) / 16 * 16;
-        return n * stage_max + tab + n * dd::kStageMeta + g0.zero_bytes + 16 * n;
-    };
+    auto smem_for = [&](int64_t n) { return dd::ring_smem(g0, stage_max, (int)n); };
     int nst = 4;
     while (nst > 2 && smem_for(nst) > dd::kMaxSmem)
         --nst;
@@ -203,13 +198,13 @@ dd_status start(dd_server_s *v) {
     v->threads = g0.threads;
     v->stage_max = (int)stage_max;
     v->zero_bytes = g0.zero_bytes;
+    v->builders = g0.builders;
 
     v->in_pitch = (int64_t)round16((size_t)SB_max * v->elem) / v->elem;
     v->out_pitch = (B_max + 3) / 4 * 4;
     v->in_bytes = (size_t)nchan_max * v->in_pitch * v->elem;
-    v->planes_bytes = (size_t)(v->nph - 1) * v->in_bytes;
     v->out_bytes = (size_t)ndm_max * v->out_pitch * sizeof(float);
-    const size_t slot_bytes = v->in_bytes + v->planes_bytes + v->out_bytes;
+    const size_t slot_bytes = v->in_bytes + v->out_bytes;
     const int64_t room = (int64_t)v->budget - tails;
     const int64_t by_budget = room > 0 ? room / (int64_t)slot_bytes : 0;
     const int nslots = (int)std::min<int64_t>(v->max_inflight, by_budget);
@@ -228,8 +223,6 @@ dd_status start(dd_server_s *v) {
     v->slots.resize(nslots);
     for (auto &s : v->slots) {
         ok = ok && cudaMalloc(&s.in, v->in_bytes) == cudaSuccess;
-        if (v->planes_bytes)
-            ok = ok && cudaMalloc(&s.planes, v->planes_bytes) == cudaSuccess;
         ok = ok && cudaMalloc((void **)&s.out, v->out_bytes) == cudaSuccess;
     }
     const int nstaging = 2 * nslots;
@@ -293,21 +286,12 @@ dd_status launch_batch(dd_server_s *v, Lane &l, const std::vector<dd_ticket> &ti
         if (e == cudaSuccess)
             e = cudaEventRecord(b.tail_ready, s);
         b.tail_valid = true;
-        // phase planes of the slot
-        if (e == cudaSuccess && v->dtype == DD_U8)
-            e = dd::launch_planes_u8(in, pitch_b, nchan, b.S + b.B, (uint8_t *)sl.planes,
-                                     (int64_t)nchan * pitch_b, s);
-        else if (e == cudaSuccess && v->dtype == DD_F16)
-            e = dd::launch_planes_f16(in, pitch_b, nchan, b.S + b.B, (uint8_t *)sl.planes,
-                                      (int64_t)nchan * pitch_b, s);
         dd::DevTables *dt = nullptr;
         dd::device_tables(b.plan, &dt);
         dd::BeamArgs &d = l.h_desc[i];
         d = dd::BeamArgs{};
         d.in = in;
         d.in_pitch_b = (int64_t)pitch_b;
-        d.planes = static_cast<const uint8_t *>(sl.planes);
-        d.plane_stride = (int64_t)nchan * (int64_t)pitch_b;
         d.nsamp_in = b.S + b.B;
         d.out = sl.out;
         d.out_pitch = v->out_pitch;
@@ -339,6 +323,7 @@ dd_status launch_batch(dd_server_s *v, Lane &l, const std::vector<dd_ticket> &ti
     a.nstages = v->nst;
     a.stage_bytes = v->stage_max;
     a.zero_bytes = v->zero_bytes;
+    a.builders = v->builders;
     a.one = 1u;
     a.status = v->d_status;
     const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(tile0, v->nsm));
@@ -350,7 +335,7 @@ dd_status launch_batch(dd_server_s *v, Lane &l, const std::vector<dd_ticket> &ti
     }
     if (e != cudaSuccess)
         return fail(DD_ERR_CUDA, std::string("server kernel launch: ") + cudaGetErrorString(e));
-    dd::count_launch((int)rs.size() * (v->dtype == DD_F32 ? 0 : 1) + 1);
+    dd::count_launch(1);
     // results into the callers' buffers
     for (size_t i = 0; i < rs.size() && e == cudaSuccess; ++i) {
         SrvReq &r = *rs[i];
@@ -532,7 +517,6 @@ dd_status dd_server_create(size_t hbm_budget_bytes, int max_inflight, dd_dtype d
     v->max_inflight = max_inflight;
     v->dtype = dtype;
     v->elem = dd::elem_size(dtype);
-    v->nph = dd::phases(dtype);
     *out = v;
     return DD_OK;
 }

@@ -57,11 +57,25 @@ def test_noalloc_matches_execute_twice(dd, kind):
             assert np.all(np.abs(got.astype(np.float64) - want) <= 1e-6 * asum), f"call {call}"
 
 
-def test_noalloc_rejects_inputs_beyond_its_fixed_scratch(dd):
-    plan = dd.Plan(1024, 1500.0, -0.29296875, 64e-6, np.arange(16, dtype=np.float32))
-    nin = 40000                   # 3 phase planes x 1024 x 40000 B > 64 MiB
-    x = torch.zeros((1024, nin), dtype=torch.uint8, device="cuda")
-    out = torch.empty((16, 1024), dtype=torch.float32, device="cuda")
+def test_noalloc_takes_large_inputs_and_rejects_tables_beyond_its_array(dd, oracle_lib):
+    # The input size is not limited: 1024 channels x 40000 samples of uint8.
+    rng = np.random.default_rng(405)
+    dms = np.arange(16, dtype=np.float32)
+    plan = dd.Plan(1024, 1500.0, -0.29296875, 64e-6, dms)
+    nin = 40000
+    data = fb.random_filterbank(rng, 1024, nin, "u8", pitch=nin)
+    x = torch.from_numpy(data).cuda()
+    nsamp_out = nin - plan.maxshift
+    got = _plane(plan, plan.execute_noalloc_ptr, x, nin, nin, nsamp_out, 0)
+    table = oracle_lib.dmshift(1024, 1500.0, -0.29296875, 64e-6)
+    d = rng.integers(0, 16, size=64)
+    t = rng.integers(0, nsamp_out, size=64)
+    want, _ = oracle_lib.dedisperse_cells(data, table, dms, d, t)
+    assert np.array_equal(got[d, t].astype(np.float64), want)
+    # 140000 DMs: 2 x 4 x 140096 bytes of DM tables exceed the fixed 1 MiB.
+    big = dd.Plan(16, 1500.0, -1.0, 64e-6, np.linspace(0.0, 1.0, 140000, dtype=np.float32))
+    x = torch.zeros((16, 1024), dtype=torch.uint8, device="cuda")
+    out = torch.empty((140000, 512), dtype=torch.float32, device="cuda")
     with pytest.raises(dd.DDError) as e:
-        plan.execute_noalloc_ptr(x.data_ptr(), 0, nin, nin, out.data_ptr(), 1024, 1024)
+        big.execute_noalloc_ptr(x.data_ptr(), 0, 1024, 1024, out.data_ptr(), 512, 512)
     assert e.value.status == -1 and "fixed" in str(e.value)
