@@ -624,7 +624,19 @@ __global__ void __launch_bounds__(32 * (max_consumer_warps(DT, NW) + 1 + (ELEM <
         }
     };
 
-    auto load_words = [&](int2 off, uint32_t (&x)[NW], uint32_t (&y)[NW]) {
+    // One register buffer of words per row (x: row 2q, y: row 2q+1).  Each
+    // iteration (channel pair q, DM j) sums its words and, word by word,
+    // reloads the buffer with the next iteration's words, so every load is
+    // issued one iteration before its use with half the registers of a
+    // double buffer.  The next iteration's table offsets are themselves
+    // read one iteration earlier still (`on`).
+    uint32_t x[NW], y[NW];
+    // Offsets of rows 2q, 2q+1 for DM j, in the table of a stage (tb points
+    // at this thread's first DM column).
+    auto off2 = [&](const int *tb, int q, int j) {
+        return *reinterpret_cast<const int2 *>(tb + (q * dm_cta + j) * 2);
+    };
+    auto load_words = [&](int2 off) {
         const uint32_t *p0 = reinterpret_cast<const uint32_t *>(smem + off.x + thr_off);
         const uint32_t *p1 = reinterpret_cast<const uint32_t *>(smem + off.y + thr_off);
 #pragma unroll
@@ -633,11 +645,11 @@ __global__ void __launch_bounds__(32 * (max_consumer_warps(DT, NW) + 1 + (ELEM <
             y[k] = p1[32 * k];
         }
     };
-    // Offsets of rows 2q, 2q+1 of stage buffer b for this thread's DM j.
-    auto offsets = [&](int b, int q, int j) {
-        return *reinterpret_cast<const int2 *>(atab + b * tab_stride + (q * dm_cta + kw + j) * 2);
-    };
-    auto accumulate = [&](int j, const uint32_t (&x)[NW], const uint32_t (&y)[NW]) {
+    // Sum the words of this iteration into DM j; if `reload`, refill each
+    // word from the next iteration's rows (offsets nxt) right after use.
+    auto sum_reload = [&](int j, bool reload, int2 nxt) {
+        const uint32_t *p0 = reinterpret_cast<const uint32_t *>(smem + nxt.x + thr_off);
+        const uint32_t *p1 = reinterpret_cast<const uint32_t *>(smem + nxt.y + thr_off);
 #pragma unroll
         for (int k = 0; k < NW; ++k) {
             if (ELEM == 1) {
@@ -651,82 +663,95 @@ __global__ void __launch_bounds__(32 * (max_consumer_warps(DT, NW) + 1 + (ELEM <
                 P[j][k][0] = __fadd_rn(__fadd_rn(P[j][k][0], __uint_as_float(x[k])),
                                        __uint_as_float(y[k]));
             }
+            if (reload) {
+                x[k] = p0[32 * k];
+                y[k] = p1[32 * k];
+            }
         }
     };
 
-    // Stages run in ring order; within a stage the iterations (channel pair q,
-    // DM j) run in order and the words of the next iteration are loaded into
-    // the other register buffer before the current ones are summed.  The pair
-    // loop is unrolled by two, so the buffers alternate with the
-    // (compile-time) parity of the iteration.
-    const int npairs = cstage / 2;  // even: chan_per_stage is a multiple of 4
-    uint32_t xa[NW], ya[NW], xb[NW], yb[NW];
+    // Stages run in ring order.  Within a stage of T = npairs*DT iterations
+    // the words of iteration i+1 are loaded during iteration i and the
+    // offsets of iteration i+2 are read during iteration i.  When the next
+    // stage continues the tile without a widening in between, both reach
+    // into it: the consumer waits for that stage at iteration T-2 and
+    // releases the current one at T-1, after its last loads from it.
+    // Otherwise the next stage starts fresh, so no prefetched buffer is live
+    // across a widening.
+    const int npairs = cstage / 2;  // >= 2: chan_per_stage is a multiple of 4
+    // Pairs whose iterations never reach past the stage (i + 2 < T).
+    const int q_plain = npairs - (DT == 1 ? 2 : 1);
+    bool prefetched = false;
+    int2 on = make_int2(0, 0);  // offsets of the next iteration
     for (int64_t g = 0;; ++g) {
         const int b = (int)(g % nst);
-        if (!mbar_wait(full0 + 8 * b, (uint32_t)((g / nst) & 1))) {
+        if (!prefetched && !mbar_wait(full0 + 8 * b, (uint32_t)((g / nst) & 1))) {
             record(a.status, kDevTimeout);
             return;
         }
         const StageMeta m = meta[b];
         if (m.beam < 0)
             break;  // no further tile
+        const int *tb = atab + b * tab_stride + 2 * kw;
         if (m.st == 0) {
             beam = m.beam;
             kthr = m.td * dm_cta + kw;
             tw = m.t0 + (int64_t)wti * SPAN;
             since_flush = 0;
             flushed_once = false;
-            load_words(offsets(b, 0, 0), xa, ya);
+        }
+        if (!prefetched) {
+            load_words(off2(tb, 0, 0));
+            on = off2(tb, 1 / DT, 1 % DT);
         }
         since_flush += cstage;
         const bool last = m.st + 1 == m.nstage;
         // Widen (uint8) or close a compensated block (floats) after this stage
-        // if the next one would overflow it.  The next stage's first words are
-        // then loaded after the widening, so no prefetched buffer is live
-        // across it.
+        // if the next one would overflow it.
         const bool widen = !last && since_flush + cstage > FLUSH;
-        for (int q = 0; q < npairs; q += 2) {
+        const bool cross = !last && !widen;
+        const int bn = (int)((g + 1) % nst);
+        const int *tbn = atab + bn * tab_stride + 2 * kw;
+        for (int q = 0; q < q_plain; ++q) {
 #pragma unroll
-            for (int i = 0; i < 2 * DT; ++i) {
-                uint32_t (&cx)[NW] = (i & 1) ? xb : xa;
-                uint32_t (&cy)[NW] = (i & 1) ? yb : ya;
-                uint32_t (&nx)[NW] = (i & 1) ? xa : xb;
-                uint32_t (&ny)[NW] = (i & 1) ? ya : yb;
-                const int j = i % DT;
-                if (i + 1 < 2 * DT) {
-                    load_words(offsets(b, q + (i + 1) / DT, (i + 1) % DT), nx, ny);
-                } else if (q + 2 < npairs) {
-                    load_words(offsets(b, q + 2, 0), nx, ny);
-                } else {
-                    // The words of this stage's last iteration are in registers:
-                    // release the stage before summing them.
+            for (int j = 0; j < DT; ++j) {
+                const int2 onn = off2(tb, q + (j + 2) / DT, (j + 2) % DT);
+                sum_reload(j, true, on);
+                on = onn;
+            }
+        }
+        for (int q = q_plain; q < npairs; ++q) {
+#pragma unroll
+            for (int j = 0; j < DT; ++j) {
+                const int left = (npairs - q) * DT - j;  // iterations left, this one included
+                int2 onn = on;
+                if (left > 2) {
+                    onn = off2(tb, q + (j + 2) / DT, (j + 2) % DT);
+                } else if (cross) {
+                    if (left == 2 &&
+                        !mbar_wait(full0 + 8 * bn, (uint32_t)(((g + 1) / nst) & 1))) {
+                        record(a.status, kDevTimeout);
+                        return;
+                    }
+                    onn = off2(tbn, (2 - left) / DT, (2 - left) % DT);
+                }
+                if (left == 1) {
+                    // Every load from this stage has been issued: release it.
                     __syncwarp();
                     if (lane == 0)
                         mbar_arrive(empty0 + 8 * b);
-                    if (!last && !widen) {
-                        const int bn = (int)((g + 1) % nst);
-                        if (!mbar_wait(full0 + 8 * bn, (uint32_t)(((g + 1) / nst) & 1))) {
-                            record(a.status, kDevTimeout);
-                            return;
-                        }
-                        load_words(offsets(bn, 0, 0), nx, ny);
-                    }
                 }
-                accumulate(j, cx, cy);
+                sum_reload(j, left > 1 || cross, on);
+                on = onn;
             }
         }
+        prefetched = cross;
         if (widen) {
             if (ELEM == 1)
                 flush_u8();
             else
                 block_float();
             since_flush = 0;
-            const int bn = (int)((g + 1) % nst);  // 2*DT iterations per pair step: next is xa/ya
-            if (!mbar_wait(full0 + 8 * bn, (uint32_t)(((g + 1) / nst) & 1))) {
-                record(a.status, kDevTimeout);
-                return;
-            }
-            load_words(offsets(bn, 0, 0), xa, ya);
         }
         if (last) {
             if (ELEM == 1) {
