@@ -636,6 +636,25 @@ __global__ void __launch_bounds__(32 * (max_consumer_warps(DT, NW) + 1 + (ELEM <
     auto off2 = [&](const int *tb, int q, int j) {
         return *reinterpret_cast<const int2 *>(tb + (q * dm_cta + j) * 2);
     };
+    // Offsets of DMs j and j+1 (j even; DT even keeps the int4 16-byte aligned).
+    auto off4 = [&](const int *tb, int q, int j) {
+        return *reinterpret_cast<const int4 *>(tb + (q * dm_cta + j) * 2);
+    };
+    int2 hold = make_int2(0, 0);  // DM j+1 half of the last off4
+    // Offsets of iteration (q, j) read two iterations ahead: an even j reads
+    // the pair (j, j+1) and keeps the odd half for the next iteration.
+    auto ahead = [&](const int *tb, int q, int j) {
+        if constexpr (DT % 2 == 0) {
+            if ((j & 1) == 0) {
+                const int4 o = off4(tb, q, j);
+                hold = make_int2(o.z, o.w);
+                return make_int2(o.x, o.y);
+            }
+            return hold;
+        } else {
+            return off2(tb, q, j);
+        }
+    };
     auto load_words = [&](int2 off) {
         const uint32_t *p0 = reinterpret_cast<const uint32_t *>(smem + off.x + thr_off);
         const uint32_t *p1 = reinterpret_cast<const uint32_t *>(smem + off.y + thr_off);
@@ -701,8 +720,14 @@ __global__ void __launch_bounds__(32 * (max_consumer_warps(DT, NW) + 1 + (ELEM <
             flushed_once = false;
         }
         if (!prefetched) {
-            load_words(off2(tb, 0, 0));
-            on = off2(tb, 1 / DT, 1 % DT);
+            if constexpr (DT % 2 == 0) {
+                const int4 o = off4(tb, 0, 0);
+                load_words(make_int2(o.x, o.y));
+                on = make_int2(o.z, o.w);
+            } else {
+                load_words(off2(tb, 0, 0));
+                on = off2(tb, 1, 0);
+            }
         }
         since_flush += cstage;
         const bool last = m.st + 1 == m.nstage;
@@ -715,7 +740,7 @@ __global__ void __launch_bounds__(32 * (max_consumer_warps(DT, NW) + 1 + (ELEM <
         for (int q = 0; q < q_plain; ++q) {
 #pragma unroll
             for (int j = 0; j < DT; ++j) {
-                const int2 onn = off2(tb, q + (j + 2) / DT, (j + 2) % DT);
+                const int2 onn = ahead(tb, q + (j + 2) / DT, (j + 2) % DT);
                 sum_reload(j, true, on);
                 on = onn;
             }
@@ -726,14 +751,14 @@ __global__ void __launch_bounds__(32 * (max_consumer_warps(DT, NW) + 1 + (ELEM <
                 const int left = (npairs - q) * DT - j;  // iterations left, this one included
                 int2 onn = on;
                 if (left > 2) {
-                    onn = off2(tb, q + (j + 2) / DT, (j + 2) % DT);
+                    onn = ahead(tb, q + (j + 2) / DT, (j + 2) % DT);
                 } else if (cross) {
                     if (left == 2 &&
                         !mbar_wait(full0 + 8 * bn, (uint32_t)(((g + 1) / nst) & 1))) {
                         record(a.status, kDevTimeout);
                         return;
                     }
-                    onn = off2(tbn, (2 - left) / DT, (2 - left) % DT);
+                    onn = ahead(tbn, (2 - left) / DT, (2 - left) % DT);
                 }
                 if (left == 1) {
                     // Every load from this stage has been issued: release it.
