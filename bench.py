@@ -42,6 +42,29 @@ SM_COUNT = 152
 ADD_LANES_PER_SM = 128  # FP32/INT32 lanes per SM per clock
 
 
+# DRAM traffic of one de-dispersion launch from an ncu capture
+# (dram__bytes_read.sum + dram__bytes_write.sum), valid only for the kernel
+# source it was taken on (sha256 of csrc/dd_kernel.cuh) and the same workload,
+# dtype and tile shape; any other run reports traffic null.
+PROFILED_TRAFFIC = [
+    {"workload": "lband-1024ch-1024dm-131072", "dtype": "u8", "tiles": [4, 12, 1, 8, 8],
+     "kernel_sha256": "bbb320f94891bc8e26f584efa6df2a383557ca8287901e441875502a47c35220",
+     "bytes": 152856064 + 520188160, "source": "profiles/dedisperse_lband_u8_full.md"},
+]
+
+
+def profiled_traffic(workload: str, dtype: str, tiles) -> dict | None:
+    import hashlib
+    path = os.path.join(ROOT, "paper_1111_6399_gb300", "csrc", "dd_kernel.cuh")
+    with open(path, "rb") as f:
+        digest = hashlib.sha256(f.read()).hexdigest()
+    for rec in PROFILED_TRAFFIC:
+        if (rec["kernel_sha256"] == digest and rec["workload"] == workload
+                and rec["dtype"] == dtype and list(rec["tiles"]) == list(tiles)):
+            return rec
+    return None
+
+
 def peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -465,6 +488,7 @@ def run_ours(args, w):
     clocks = clk.summary()
     peak_adds = add_peak(pk.get("sm_max_mhz", 2070.0))
     achieved = adds / (kernel_ms / 1e3)
+    prof = profiled_traffic(w.name, dt, plan.get_tiles(dt))
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
@@ -477,7 +501,10 @@ def run_ours(args, w):
                          % (w.nchan * nin * host.itemsize / 1e6, w.ndm * w.nsamp_out * 4 / 1e6),
                    "parallelism": f"replicas{world}" if world > 1 else "single-gpu"},
         "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_adds / 1e12,
-                     "unit": "Tadd/s", "frac": achieved / peak_adds, "traffic": None,
+                     "unit": "Tadd/s", "frac": achieved / peak_adds,
+                     "traffic": prof["bytes"] if prof else None,
+                     "traffic_unit": "bytes per launch (ncu dram read + write)",
+                     "traffic_source": prof["source"] if prof else None,
                      "peak_source": f"{SM_COUNT} SMs x {ADD_LANES_PER_SM} lanes x "
                                     f"{pk.get('sm_max_mhz', 2070.0):.0f} MHz ({pk_kind} max clock)",
                      "kernel": "dedisperse_kernel<%d,%d,%d>" % (
