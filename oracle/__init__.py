@@ -79,6 +79,11 @@ def _lib(omp: bool = False) -> ctypes.CDLL:
             lib.oracle_dedisperse_cells.argtypes = [p, ctypes.c_int, ctypes.c_int, i64, p, p,
                                                     i64, p, p, p, p]
             lib.oracle_dedisperse_cells.restype = None
+            lib.oracle_unpack.argtypes = [p, ctypes.c_int, ctypes.c_int, i64, p, i64]
+            lib.oracle_unpack.restype = None
+            lib.oracle_detect.argtypes = [p, ctypes.c_int, i64, i64, ctypes.c_int, ctypes.c_int,
+                                          p, p, p, p]
+            lib.oracle_detect.restype = None
             _LIBS[omp] = lib
         return _LIBS[omp]
 
@@ -190,3 +195,34 @@ def dedisperse_cells(data: np.ndarray, table: np.ndarray, dms: np.ndarray,
                                           _ptr(dms), len(d_idx), _ptr(d_idx), _ptr(t_idx),
                                           _ptr(out), _ptr(asum))
     return out, asum
+
+
+def unpack(raw: np.ndarray, nbits: int, nchan: int, nsamp: int) -> np.ndarray:
+    """Corner turn of nsamp sigproc-order spectra of nchan nbits-bit samples
+    (first sample in the lowest bits of a byte) into uint8 [nchan][nsamp]."""
+    raw = np.ascontiguousarray(raw, dtype=np.uint8)
+    if nbits not in (1, 2, 4, 8) or (nchan * nbits) % 8:
+        raise ValueError("nbits must be 1, 2, 4 or 8 and nchan*nbits a multiple of 8")
+    if raw.size < nsamp * nchan * nbits // 8:
+        raise ValueError("input shorter than nsamp spectra")
+    out = np.empty((nchan, nsamp), dtype=np.uint8)
+    _lib().oracle_unpack(_ptr(raw), nbits, nchan, nsamp, _ptr(out), nsamp)
+    return out
+
+
+def detect(plane: np.ndarray, nlevels: int, integer_valued: bool):
+    """Boxcar search of every DM row of a (DM,t) plane over widths 1, 2, ...,
+    2^(nlevels-1) (the rules are in the C file).  Returns (mean[ndm], std[ndm],
+    snr[ndm][nlevels], t[ndm][nlevels])."""
+    x = np.ascontiguousarray(plane, dtype=np.float64)
+    ndm, nsamp = x.shape
+    if integer_valued and (np.any(x != np.floor(x)) or np.any(x < 0) or np.any(x >= 2 ** 21)
+                           or nsamp > 2 ** 21):
+        raise ValueError("integer mode needs integers in [0, 2^21) and nsamp <= 2^21")
+    mean = np.empty(ndm, dtype=np.float64)
+    std = np.empty(ndm, dtype=np.float64)
+    snr = np.empty((ndm, nlevels), dtype=np.float64)
+    tpk = np.empty((ndm, nlevels), dtype=np.int64)
+    _lib().oracle_detect(_ptr(x), ndm, nsamp, nsamp, nlevels, int(bool(integer_valued)),
+                         _ptr(mean), _ptr(std), _ptr(snr), _ptr(tpk))
+    return mean, std, snr, tpk

@@ -192,3 +192,111 @@ void oracle_dedisperse_cells(const void *in, int elem, int nchan, int64_t in_pit
         }
     }
 }
+
+/*
+ * Input side: corner turn and bit unpacking.  The paper's test data are
+ * sigproc filterbanks (Sec. 2, Fig. 1).  A filterbank block in that layout
+ * stores nsamp spectra one after another, each holding nchan samples of
+ * nbits bits (1, 2, 4 or 8).  Samples
+ * are packed in time-then-channel order, filling each byte from its lowest
+ * bits: channel c of spectrum t occupies bits (t*nchan + c)*nbits onwards,
+ * where bit b is bit (b mod 8) of byte b/8.  nchan*nbits is a multiple of 8,
+ * so every spectrum starts on a byte.  The de-dispersion reads channel rows,
+ * so the block is turned into out[c][t]; sample values are kept as they are
+ * (0 .. 2^nbits - 1).
+ */
+void oracle_unpack(const uint8_t *in, int nbits, int nchan, int64_t nsamp, uint8_t *out,
+                   int64_t out_pitch)
+{
+    const unsigned mask = (1u << nbits) - 1u;
+    for (int64_t t = 0; t < nsamp; ++t)
+        for (int c = 0; c < nchan; ++c) {
+            const int64_t bit = (t * nchan + c) * (int64_t)nbits;
+            out[(int64_t)c * out_pitch + t] = (uint8_t)((in[bit / 8] >> (bit % 8)) & mask);
+        }
+}
+
+/*
+ * Detection on the (DM,t) plane.  Sec. 4 and Fig. 3 of the paper search the
+ * plane for a simulated pulse and recover it at its DM and time; the paper
+ * gives no detection formula.  Reading adopted here (matched boxcar filters
+ * with a per-DM noise estimate):
+ *
+ *   for each DM row x[0..nsamp):
+ *     mean = S1/n and std = sqrt(S2/n - mean^2) (0 if negative), n = nsamp,
+ *       S1 = sum x, S2 = sum x^2;
+ *     for each width w = 2^l, l = 0..nlevels-1, and t = 0..nsamp-w:
+ *       B(t) = sum_{k<w} x[t+k];
+ *     peak t = the first t with the largest B(t);
+ *     snr = (B(peak) - w*mean) / (std*sqrt(w)), 0 if std == 0;
+ *     if nsamp < w there is no window: t = -1, snr = -infinity.
+ *
+ * Sums over an integer-valued plane (integer_valued != 0; values in
+ * [0, 2^21), nsamp <= 2^21) are exact: S1, S2 and B in 64-bit integers,
+ * converted to FP64 once.  Otherwise S1, S2 and B are FP64 sums in index
+ * order.  Every FP64 step is one IEEE operation (built without contraction).
+ */
+void oracle_detect(const double *plane, int ndm, int64_t pitch, int64_t nsamp, int nlevels,
+                   int integer_valued, double *mean_out, double *std_out, double *snr_out,
+                   int64_t *t_out)
+{
+    const double n = (double)nsamp;
+    for (int d = 0; d < ndm; ++d) {
+        const double *x = plane + (int64_t)d * pitch;
+        double s1, s2;
+        if (integer_valued) {
+            uint64_t i1 = 0, i2 = 0;
+            for (int64_t t = 0; t < nsamp; ++t) {
+                const uint64_t v = (uint64_t)x[t];
+                i1 += v;
+                i2 += v * v;
+            }
+            s1 = (double)i1;
+            s2 = (double)i2;
+        } else {
+            s1 = 0.0;
+            s2 = 0.0;
+            for (int64_t t = 0; t < nsamp; ++t) {
+                s1 += x[t];
+                s2 += x[t] * x[t];
+            }
+        }
+        const double mean = s1 / n;
+        double var = s2 / n - mean * mean;
+        if (var < 0.0)
+            var = 0.0;
+        const double sd = sqrt(var);
+        mean_out[d] = mean;
+        std_out[d] = sd;
+        for (int l = 0; l < nlevels; ++l) {
+            const int64_t w = (int64_t)1 << l;
+            int64_t best_t = -1;
+            double best = 0.0;
+            for (int64_t t = 0; t + w <= nsamp; ++t) {
+                double b;
+                if (integer_valued) {
+                    uint64_t ib = 0;
+                    for (int64_t k = 0; k < w; ++k)
+                        ib += (uint64_t)x[t + k];
+                    b = (double)ib;
+                } else {
+                    b = 0.0;
+                    for (int64_t k = 0; k < w; ++k)
+                        b += x[t + k];
+                }
+                if (best_t < 0 || b > best) {
+                    best = b;
+                    best_t = t;
+                }
+            }
+            t_out[(int64_t)d * nlevels + l] = best_t;
+            if (best_t < 0)
+                snr_out[(int64_t)d * nlevels + l] = -INFINITY;
+            else if (sd == 0.0)
+                snr_out[(int64_t)d * nlevels + l] = 0.0;
+            else
+                snr_out[(int64_t)d * nlevels + l] =
+                    (best - (double)w * mean) / (sd * sqrt((double)w));
+        }
+    }
+}
