@@ -256,6 +256,39 @@ def batch_section(dd, torch, dev, steps: int, tiles=None):
     return res
 
 
+def unpack_section(dd, torch, dev, w: fb.Workload, nin: int, hbm_gbs: float, reps: int = 20):
+    """dd_unpack on one beam's worth of sigproc spectra (nin spectra of
+    w.nchan channels) at 8, 4, 2 and 1 bits: HBM-bound, bytes read + written
+    per launch over CUDA-event time, against the measured copy bandwidth.
+    Each launch moves more than L2 holds except at 1-2 bits, where the timed
+    launches alternate between two input/output pairs."""
+    res = {"workload": f"{nin} spectra x {w.nchan} channels -> uint8 [{w.nchan}][{nin}]",
+           "bound": "hbm", "peak_gbs": hbm_gbs}
+    pitch = (nin + 15) // 16 * 16
+    g = torch.Generator(device=dev)
+    g.manual_seed(6)
+    outs = [torch.empty((w.nchan, pitch), dtype=torch.uint8, device=dev) for _ in range(2)]
+    for nbits in (8, 4, 2, 1):
+        nbytes = nin * w.nchan * nbits // 8
+        raws = [torch.randint(0, 256, (nbytes,), dtype=torch.uint8, device=dev, generator=g)
+                for _ in range(2)]
+        for i in range(3):
+            dd.unpack(raws[i % 2], nbits, w.nchan, nin, outs[i % 2])
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        for i in range(reps):
+            dd.unpack(raws[i % 2], nbits, w.nchan, nin, outs[i % 2])
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        moved = nbytes + w.nchan * nin
+        res[f"{nbits}bit"] = {"ms": ms, "gbs": moved / ms / 1e6,
+                              "frac": moved / ms / 1e6 / hbm_gbs, "bytes": moved}
+        del raws
+    return res
+
+
 def serving_section(dd, torch, dev, seconds: float = 8.0, speed: float = 1.25):
     """128 streaming L-band beams (1024 channels, 1024 DMs, blocks of 65536
     samples = 4.194 s) served with continuous batching: Poisson arrivals at
@@ -528,6 +561,8 @@ def run_ours(args, w):
                                       plan.get_tiles(dt) if dt == "u8" else None)
     if not args.no_serve and world == 1:
         line["serving"] = serving_section(dd, torch, dev)
+    if not args.no_unpack and world == 1:
+        line["unpack"] = unpack_section(dd, torch, dev, w, nin, pk.get("hbm_gbs", 6800.0))
     if not args.no_cpu:
         line["cpu_baseline"] = cpu_oracle_sample(w)
     print(json.dumps(line), flush=True)
@@ -548,6 +583,7 @@ def main():
                     help="storage type of the beam (the same integer noise)")
     ap.add_argument("--no-batch", action="store_true", help="skip the 64-beam batch section")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving section")
+    ap.add_argument("--no-unpack", action="store_true", help="skip the input unpacking section")
     ap.add_argument("--tiles", default="", help="fixed tile shape dthr,dm_warps,time_warps,cstage")
     args = ap.parse_args()
     w = WORKLOADS[args.workload]

@@ -187,6 +187,24 @@ dd_status dd_execute_noalloc(dd_plan_t plan, const void *in, dd_dtype dtype, int
                              int64_t nsamp_in, float *out, int64_t out_pitch,
                              int64_t nsamp_out, void *stream);
 
+/* --- input side: corner turn and bit unpacking ---------------------------- */
+
+/* Turn a block of filterbank spectra into the channel rows that dd_execute
+ * reads.  The paper's test data are sigproc filterbanks (Sec. 2, Fig. 1):
+ * nsamp spectra follow one another, each holding nchan samples of nbits bits
+ * (1, 2, 4 or 8), packed in channel order from the lowest bit of each byte
+ * (channel c of spectrum t starts at bit (t*nchan + c)*nbits of the block;
+ * bit b is bit b%8 of byte b/8).
+ *   in:  device pointer to nsamp*nchan*nbits/8 bytes; any alignment (16-byte
+ *        aligned input whose spectra are multiples of 16 bytes is faster).
+ *   out: device uint8 [nchan][out_pitch], 16-byte aligned, out_pitch >= nsamp
+ *        and a multiple of 16; out[c][t] = the sample (0 .. 2^nbits - 1, not
+ *        rescaled).  Columns t >= nsamp are left untouched.
+ * nchan*nbits must be a multiple of 8 (whole-byte spectra).  Asynchronous on
+ * stream; returns DD_ERR_INVALID (nothing launched) for bad arguments. */
+dd_status dd_unpack(const void *in, int nbits, int nchan, int64_t nsamp, uint8_t *out,
+                    int64_t out_pitch, void *stream);
+
 /* --- batches: uneven beams in one persistent launch ------------------------ */
 
 typedef struct dd_batch_s *dd_batch_t;

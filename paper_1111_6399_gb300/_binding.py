@@ -30,7 +30,7 @@ EXPORTS = [
     "dd_batch_set_io", "dd_batch_execute", "dd_batch_get_tiles", "dd_batch_set_tiles",
     "dd_batch_autotune", "dd_batch_sync", "dd_server_create", "dd_server_add_beam",
     "dd_submit", "dd_poll", "dd_server_drain", "dd_server_get_stats", "dd_server_destroy",
-    "dd_selftest_wait_timeout", "dd_server_set_batch_window",
+    "dd_selftest_wait_timeout", "dd_server_set_batch_window", "dd_unpack",
 ]
 
 
@@ -85,6 +85,7 @@ def _load() -> ctypes.CDLL:
         "dd_execute_host": (i32, [p, p, i32, i64, i64, p, i64, i64]),
         "dd_execute_noalloc": (i32, [p, p, i32, i64, i64, p, i64, i64, p]),
         "dd_sync": (i32, [p, p]),
+        "dd_unpack": (i32, [p, i32, i32, i64, p, i64, p]),
         "dd_profile_events": (None, [p, p]),
         "dd_autotune": (i32, [p, p, i32, i64, i64, p, i64, i64, p, i32,
                               ctypes.POINTER(TuneResult), i32, ctypes.POINTER(i32)]),
@@ -145,6 +146,21 @@ def warp_span(code: int, words: int = 8) -> int:
 
 def launch_count() -> int:
     return int(lib.dd_launch_count())
+
+
+def unpack(raw, nbits: int, nchan: int, nsamp: int, out, stream=None) -> None:
+    """dd_unpack on torch CUDA tensors: raw holds nsamp sigproc-order spectra of
+    nchan nbits-bit samples (any dtype, contiguous bytes); out is a uint8
+    [nchan][pitch] tensor with contiguous rows.  Asynchronous on stream."""
+    import torch
+    if not (raw.is_cuda and out.is_cuda):
+        raise ValueError("dd_unpack takes CUDA tensors")
+    if out.dtype != torch.uint8 or out.dim() != 2 or out.stride(1) != 1 or not raw.is_contiguous():
+        raise ValueError("out must be a 2-D uint8 tensor with contiguous rows; raw contiguous")
+    s = torch.cuda.current_stream(out.device) if stream is None else stream
+    check(lib.dd_unpack(ctypes.c_void_p(raw.data_ptr()), int(nbits), int(nchan), int(nsamp),
+                        ctypes.c_void_p(out.data_ptr()), out.stride(0),
+                        ctypes.c_void_p(s.cuda_stream)))
 
 
 def profile_events(start=None, stop=None) -> None:

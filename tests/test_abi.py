@@ -118,6 +118,28 @@ def test_execute_validates_before_touching_a_gpu(dd):
     p.execute_ptr(0, 0, 16, 0, 0, 0, 0)
 
 
+def test_unpack_validates_before_touching_a_gpu(dd):
+    """dd_unpack argument errors are DD_ERR_INVALID from host checks alone."""
+    good = dict(inp=4096, nbits=2, nchan=64, nsamp=100, out=8192, pitch=112)
+    bad = [
+        dict(nbits=3), dict(nbits=0), dict(nbits=16),
+        dict(nchan=3),                   # 3 x 2 bits is not whole bytes
+        dict(nchan=0),
+        dict(pitch=96),                  # shorter than nsamp
+        dict(pitch=104),                 # not a multiple of 16
+        dict(nsamp=-1),
+        dict(inp=0), dict(out=0),
+        dict(out=8200),                  # output not 16-byte aligned
+    ]
+    for b in bad:
+        a = {**good, **b}
+        st = dd.lib.dd_unpack(ctypes.c_void_p(a["inp"]), a["nbits"], a["nchan"], a["nsamp"],
+                              ctypes.c_void_p(a["out"]), a["pitch"], None)
+        assert st == -1, b
+    # nsamp == 0 is a no-op and needs no device
+    assert dd.lib.dd_unpack(None, 8, 16, 0, None, 0, None) == 0
+
+
 def test_status_codes_and_messages(dd):
     with pytest.raises(dd.DDError) as e:
         dd.Plan(8, 1500.0, -1.0, 0.0, [0.0])
