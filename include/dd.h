@@ -205,6 +205,33 @@ dd_status dd_execute_noalloc(dd_plan_t plan, const void *in, dd_dtype dtype, int
 dd_status dd_unpack(const void *in, int nbits, int nchan, int64_t nsamp, uint8_t *out,
                     int64_t out_pitch, void *stream);
 
+/* --- detection: matched boxcar search of the (DM,t) plane ----------------- */
+
+/* Search every DM row of a de-dispersed plane for pulses.  Sec. 4 and Fig. 3
+ * of the paper find a simulated pulse at its DM and time; the paper gives no
+ * formula, and the library's reading is matched boxcar filters with a per-row
+ * noise estimate.  For each row x[0..nsamp):
+ *   mean = S1/n, std = sqrt(S2/n - mean^2) (0 if negative), with S1 = sum x,
+ *   S2 = sum x^2, n = nsamp;
+ *   for each width w = 2^l, l = 0..nlevels-1: the largest boxcar sum
+ *   B = x[t] + ... + x[t+w-1] over t = 0..nsamp-w, at its first t, and
+ *   snr = (B - w*mean) / (std*sqrt(w)) (0 if std is 0; t = -1 and snr = -inf
+ *   if nsamp < w).
+ * integer_valued != 0 (planes of uint8 input): every value must be an integer
+ * in [0, 2^21) and nsamp <= 2^21; the sums are then exact and the results are
+ * identical, bit for bit, to the FP64 CPU definition.  A row holding any other
+ * value reports NaN mean, std and S/N.  Otherwise sums are FP32 boxcars and
+ * FP64 row sums (order-dependent rounding).
+ *   plane: device FP32 [ndm][pitch] (4-byte aligned, pitch >= nsamp).
+ *   mean, std: device double [ndm]; snr: device double [ndm][nlevels];
+ *   t_peak: device int64 [ndm][nlevels]; all 8-byte aligned, owned by the
+ *   caller and overwritten (they also serve as the accumulators).
+ * nlevels is 1..9 (widths up to 256).  Asynchronous on stream; bad arguments
+ * return DD_ERR_INVALID with nothing launched. */
+dd_status dd_detect(const float *plane, int64_t pitch, int ndm, int64_t nsamp, int nlevels,
+                    int integer_valued, double *mean, double *std, double *snr, int64_t *t_peak,
+                    void *stream);
+
 /* --- batches: uneven beams in one persistent launch ------------------------ */
 
 typedef struct dd_batch_s *dd_batch_t;

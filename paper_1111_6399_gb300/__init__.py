@@ -7,7 +7,7 @@ the library and raises ImportError if it has not been built
 """
 from ._binding import (DD_F16, DD_F32, DD_U8, Batch, DDError, Plan, Server, Tiles, check,
                        dtype_code,
-                       elem_size, launch_count, lib, profile_events, unpack, warp_span)
+                       detect, elem_size, launch_count, lib, profile_events, unpack, warp_span)
 
 __all__ = ["Plan", "Batch", "Server", "Tiles", "DDError", "DD_U8", "DD_F16", "DD_F32", "check", "dtype_code",
-           "elem_size", "warp_span", "launch_count", "profile_events", "unpack", "lib"]
+           "elem_size", "warp_span", "launch_count", "profile_events", "unpack", "detect", "lib"]

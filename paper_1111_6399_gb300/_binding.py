@@ -30,7 +30,7 @@ EXPORTS = [
     "dd_batch_set_io", "dd_batch_execute", "dd_batch_get_tiles", "dd_batch_set_tiles",
     "dd_batch_autotune", "dd_batch_sync", "dd_server_create", "dd_server_add_beam",
     "dd_submit", "dd_poll", "dd_server_drain", "dd_server_get_stats", "dd_server_destroy",
-    "dd_selftest_wait_timeout", "dd_server_set_batch_window", "dd_unpack",
+    "dd_selftest_wait_timeout", "dd_server_set_batch_window", "dd_unpack", "dd_detect",
 ]
 
 
@@ -86,6 +86,7 @@ def _load() -> ctypes.CDLL:
         "dd_execute_noalloc": (i32, [p, p, i32, i64, i64, p, i64, i64, p]),
         "dd_sync": (i32, [p, p]),
         "dd_unpack": (i32, [p, i32, i32, i64, p, i64, p]),
+        "dd_detect": (i32, [p, i64, i32, i64, i32, i32, p, p, p, p, p]),
         "dd_profile_events": (None, [p, p]),
         "dd_autotune": (i32, [p, p, i32, i64, i64, p, i64, i64, p, i32,
                               ctypes.POINTER(TuneResult), i32, ctypes.POINTER(i32)]),
@@ -161,6 +162,29 @@ def unpack(raw, nbits: int, nchan: int, nsamp: int, out, stream=None) -> None:
     check(lib.dd_unpack(ctypes.c_void_p(raw.data_ptr()), int(nbits), int(nchan), int(nsamp),
                         ctypes.c_void_p(out.data_ptr()), out.stride(0),
                         ctypes.c_void_p(s.cuda_stream)))
+
+
+def detect(plane, nsamp: int | None = None, nlevels: int = 9, integer_valued: bool = True,
+           stream=None):
+    """dd_detect on a float32 CUDA plane [ndm][pitch]: returns CUDA tensors
+    (mean[ndm], std[ndm], snr[ndm][nlevels], t[ndm][nlevels]).  Asynchronous."""
+    import torch
+    if not plane.is_cuda or plane.dtype != torch.float32 or plane.dim() != 2 \
+            or plane.stride(1) != 1:
+        raise ValueError("plane must be a 2-D float32 CUDA tensor with contiguous rows")
+    ndm = plane.shape[0]
+    nsamp = plane.shape[1] if nsamp is None else nsamp
+    dev = plane.device
+    mean = torch.empty(ndm, dtype=torch.float64, device=dev)
+    std = torch.empty(ndm, dtype=torch.float64, device=dev)
+    snr = torch.empty((ndm, nlevels), dtype=torch.float64, device=dev)
+    tpk = torch.empty((ndm, nlevels), dtype=torch.int64, device=dev)
+    s = torch.cuda.current_stream(dev) if stream is None else stream
+    check(lib.dd_detect(ctypes.c_void_p(plane.data_ptr()), plane.stride(0), ndm, int(nsamp),
+                        int(nlevels), int(bool(integer_valued)), ctypes.c_void_p(mean.data_ptr()),
+                        ctypes.c_void_p(std.data_ptr()), ctypes.c_void_p(snr.data_ptr()),
+                        ctypes.c_void_p(tpk.data_ptr()), ctypes.c_void_p(s.cuda_stream)))
+    return mean, std, snr, tpk
 
 
 def profile_events(start=None, stop=None) -> None:

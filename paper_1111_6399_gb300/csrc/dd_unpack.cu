@@ -7,8 +7,8 @@
 // kernel reads channel rows, so a block of spectra is turned into
 // out[c][t] (one byte per sample, value kept).
 //
-// One CTA handles tiles of 128 channels x 128 spectra (grid x: channel
-// tiles; grid y strides over time tiles).  The tile's bytes are loaded
+// One CTA handles tiles of 128 channels x 128 spectra (256 for 8-bit input;
+// grid x: channel tiles; grid y strides over time tiles).  The tile's bytes are loaded
 // row by row (one row = one spectrum's bytes for those channels) with
 // coalesced 16-byte loads when every spectrum starts on 16 bytes, byte loads
 // otherwise, into shared memory rows padded to an odd number of words.  Then
@@ -27,13 +27,17 @@
 namespace {
 
 constexpr int kTileC = 128;  // channels per tile
-constexpr int kTileT = 128;  // spectra per tile
+// Spectra per tile: longer output runs per channel row help 8-bit input
+// (measured 4.5 vs 4.1 TB/s on an L-band block); narrower samples run best
+// at 128.
+__host__ __device__ constexpr int tile_t(int nbits) { return nbits == 8 ? 256 : 128; }
 
 template <int NBITS>
 __global__ void __launch_bounds__(256) unpack_kernel(const uint8_t *__restrict__ in,
                                                      int64_t spec_bytes, int nchan, int64_t nsamp,
                                                      uint8_t *__restrict__ out, int64_t out_pitch,
                                                      int64_t ntile_t, int vec) {
+    constexpr int kTileT = tile_t(NBITS);
     constexpr int SEG = kTileC * NBITS / 8;  // bytes of one spectrum in a full tile
     constexpr int STRIDE = SEG + 4;          // shared row: an odd number of 4-byte words
     constexpr uint32_t MASK = (1u << NBITS) - 1u;
@@ -99,7 +103,7 @@ __global__ void __launch_bounds__(256) unpack_kernel(const uint8_t *__restrict__
         // those bytes into one word, and a shift and mask extract the field.
         const int lq = (threadIdx.x & 31) >> 2, lc = threadIdx.x & 3;
         constexpr int NCG = SEG / 16;  // groups of 4 column words
-        for (int g = threadIdx.x >> 5; g < 4 * NCG; g += blockDim.x >> 5) {
+        for (int g = threadIdx.x >> 5; g < (kTileT / 32) * NCG; g += blockDim.x >> 5) {
             const int q = 8 * (g / NCG) + lq;
             const int cw = 4 * (g % NCG) + lc;
             if (4 * q >= rows || cw * (32 / NBITS) >= nc)
@@ -135,6 +139,7 @@ __global__ void __launch_bounds__(256) unpack_kernel(const uint8_t *__restrict__
 template <int NBITS>
 cudaError_t launch_unpack(const uint8_t *in, int64_t spec_bytes, int nchan, int64_t nsamp,
                           uint8_t *out, int64_t out_pitch, int vec, cudaStream_t s) {
+    constexpr int kTileT = tile_t(NBITS);
     const int ntc = (nchan + kTileC - 1) / kTileC;
     const int64_t ntt = (nsamp + kTileT - 1) / kTileT;
     int dev = 0, nsm = 152;

@@ -140,6 +140,30 @@ def test_unpack_validates_before_touching_a_gpu(dd):
     assert dd.lib.dd_unpack(None, 8, 16, 0, None, 0, None) == 0
 
 
+def test_detect_validates_before_touching_a_gpu(dd):
+    """dd_detect argument errors are DD_ERR_INVALID from host checks alone."""
+    P = 4096
+    good = dict(plane=P, pitch=1000, ndm=4, nsamp=1000, nlev=9, integer=1, mean=P, std=P,
+                snr=P, t=P)
+    bad = [
+        dict(nlev=0), dict(nlev=10),       # widths 1..256 only
+        dict(nsamp=0), dict(pitch=999),    # empty rows, pitch shorter than a row
+        dict(nsamp=(1 << 21) + 1, pitch=(1 << 21) + 1),   # integer planes: nsamp <= 2^21
+        dict(ndm=-1),
+        dict(plane=0), dict(mean=0), dict(snr=0), dict(t=0),
+        dict(plane=P + 2), dict(std=P + 4), # misaligned
+    ]
+    for b in bad:
+        a = {**good, **b}
+        st = dd.lib.dd_detect(ctypes.c_void_p(a["plane"]), a["pitch"], a["ndm"], a["nsamp"],
+                              a["nlev"], a["integer"], ctypes.c_void_p(a["mean"]),
+                              ctypes.c_void_p(a["std"]), ctypes.c_void_p(a["snr"]),
+                              ctypes.c_void_p(a["t"]), None)
+        assert st == -1, b
+    # no rows: a no-op that needs no device
+    assert dd.lib.dd_detect(None, 10, 0, 10, 3, 1, None, None, None, None, None) == 0
+
+
 def test_status_codes_and_messages(dd):
     with pytest.raises(dd.DDError) as e:
         dd.Plan(8, 1500.0, -1.0, 0.0, [0.0])
