@@ -599,6 +599,55 @@ def run_ours(args, w):
         dist.destroy_process_group()
 
 
+def run_sweep(args):
+    """The Fig. 4 experiments as a second workload: execution time as a
+    percentage of real time (i) over the channel count with the maximum DM at
+    200 and as many trial DMs as channels, (ii) over the maximum DM with 2000
+    channels and 2000 trial DMs.  DMs are equally spaced from 0.  The band and
+    sampling the paper does not state are the L-band beam's: 1500 MHz down by
+    300 MHz, 64 us, 2^17 output samples (8.39 s of data).  Each point is
+    autotuned, then timed as the median of 7 launches (inputs larger than L2
+    except at the smallest points, where a launch is shorter than 1 ms)."""
+    import torch
+    import paper_1111_6399_gb300 as dd
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    pool = fb.NoisePool(7)
+    fch1, bw, tsamp, nsamp_out = 1500.0, 300.0, 64e-6, 1 << 17
+    duration = nsamp_out * tsamp
+
+    def point(nchan, ndm, maxdm):
+        dms = np.linspace(0.0, maxdm, ndm).astype(np.float32)
+        plan = dd.Plan(nchan, fch1, -bw / nchan, tsamp, dms)
+        nin = nsamp_out + plan.maxshift
+        pitch = (nin + 15) // 16 * 16
+        x = torch.from_numpy(pool.rows(nchan, nin, pitch)).to(dev)
+        out = torch.empty((ndm, nsamp_out), dtype=torch.float32, device=dev)
+        plan.autotune(x, out, nsamp_in=nin, reps=1)
+        ts = []
+        for i in range(10):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            plan.execute(x, out, nsamp_in=nin)
+            e1.record()
+            torch.cuda.synchronize()
+            if i >= 3:
+                ts.append(e0.elapsed_time(e1))
+        plan.sync()
+        ms = statistics.median(ts)
+        adds = nchan * ndm * nsamp_out
+        return {"nchan": nchan, "ndm": ndm, "max_dm": maxdm, "maxshift": plan.maxshift,
+                "ms": ms, "pct_real_time": 100.0 * ms / 1e3 / duration,
+                "adds_per_s": adds / ms * 1e3, "tiles": plan.get_tiles("u8")}
+
+    res = {"metric": "execution time as % of real time (Fig. 4)", "data": "synthetic",
+           "band": "1500 MHz down 300 MHz, tsamp 64 us, 131072 samples (8.39 s)",
+           "nchan_sweep": [point(n, n, 200.0) for n in (128, 256, 512, 1024, 2048, 4096)],
+           "maxdm_sweep": [point(2000, 2000, m) for m in (50.0, 100.0, 200.0, 400.0, 800.0,
+                                                           1600.0)]}
+    print(json.dumps(res), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -614,10 +663,14 @@ def main():
     ap.add_argument("--no-serve", action="store_true", help="skip the serving section")
     ap.add_argument("--no-unpack", action="store_true", help="skip the input unpacking section")
     ap.add_argument("--no-detect", action="store_true", help="skip the detection section")
+    ap.add_argument("--sweep", action="store_true",
+                    help="run the Fig. 4 sweeps instead (one JSON line)")
     ap.add_argument("--tiles", default="", help="fixed tile shape dthr,dm_warps,time_warps,cstage")
     args = ap.parse_args()
     w = WORKLOADS[args.workload]
-    if args.impl == "reference":
+    if args.sweep:
+        run_sweep(args)
+    elif args.impl == "reference":
         run_reference(args, w)
     else:
         run_ours(args, w)
