@@ -53,10 +53,20 @@ __device__ __forceinline__ float unordered(uint32_t k) {
 // One warp's segment.  CHECK: the segment reaches the end of the row, so
 // loads and boxcar ends are checked against nsamp; interior segments (every
 // boxcar ending before nsamp) skip the checks.
+// a + b on the FMA pipe (b * one + a, one == 1 at run time): the integer ALU
+// pipe is this kernel's bottleneck.
+__device__ __forceinline__ uint32_t add_fma(uint32_t a, uint32_t b, uint32_t one) {
+    uint32_t r;
+    asm("mad.lo.u32 %0, %1, %2, %3;" : "=r"(r) : "r"(b), "r"(one), "r"(a));
+    return r;
+}
+__device__ __forceinline__ float add_fma(float a, float b, uint32_t) { return a + b; }
+
 template <bool INT, bool CHECK>
 __device__ __forceinline__ void detect_segment(const float *__restrict__ x, int64_t nsamp,
                                                int64_t s0, int row, int nlevels, int lane,
-                                               unsigned long long *s1, unsigned long long *s2,
+                                               uint32_t one, unsigned long long *s1,
+                                               unsigned long long *s2,
                                                unsigned long long *keys) {
     using T = typename std::conditional<INT, uint32_t, float>::type;
     // Positions of this lane relative to the end of the row: sample k is
@@ -93,17 +103,34 @@ __device__ __forceinline__ void detect_segment(const float *__restrict__ x, int6
     auto track = [&](int lev, int w) {
         uint32_t bv = 0;
         int bk = -1;
+        if (INT && !CHECK && lev <= 5) {
+            // Integer boxcars of width <= 32 are below 2^26, so (B << 5) | (31 - k)
+            // fits 32 bits: one multiply-add (FMA pipe) and one max per sample
+            // give the highest B at its first k.
+            const uint32_t by32 = one << 5;  // 32, opaque to the compiler
+            uint32_t best = 0;
 #pragma unroll
-        for (int k = 0; k < kOwnK; ++k) {
-            const uint32_t v = INT ? (uint32_t)z[k] : ordered((float)z[k]);
-            if (CHECK) {
-                if (32 * k + w <= lim && (bk < 0 || v > bv)) {
+            for (int k = 0; k < kOwnK; ++k) {
+                uint32_t key;
+                asm("mad.lo.u32 %0, %1, %2, %3;" : "=r"(key) : "r"((uint32_t)z[k]), "r"(by32),
+                    "r"(31u - (uint32_t)k));
+                best = max(best, key);
+            }
+            bv = best >> 5;
+            bk = 31 - (int)(best & 31u);
+        } else {
+#pragma unroll
+            for (int k = 0; k < kOwnK; ++k) {
+                const uint32_t v = INT ? (uint32_t)z[k] : ordered((float)z[k]);
+                if (CHECK) {
+                    if (32 * k + w <= lim && (bk < 0 || v > bv)) {
+                        bv = v;
+                        bk = k;
+                    }
+                } else if (k == 0 || v > bv) {
                     bv = v;
                     bk = k;
                 }
-            } else if (k == 0 || v > bv) {
-                bv = v;
-                bk = k;
             }
         }
         unsigned long long key = 0;
@@ -131,14 +158,14 @@ __device__ __forceinline__ void detect_segment(const float *__restrict__ x, int6
 #pragma unroll
             for (int k = 0; k + 1 < kKH; ++k) {
                 const T r1 = __shfl_sync(0xffffffffu, z[k + 1], src);
-                z[k] = z[k] + (wrap ? r1 : r);
+                z[k] = add_fma(z[k], wrap ? r1 : r, one);
                 r = r1;
             }
         } else {
             const int m = w / 32;
 #pragma unroll
             for (int k = 0; k + m < kKH; ++k)
-                z[k] = z[k] + z[k + m];
+                z[k] = add_fma(z[k], z[k + m], one);
         }
         track(lev, 2 * w);
     }
@@ -176,7 +203,8 @@ __global__ void __launch_bounds__(32 * kWarps, 3) detect_kernel(const float *__r
                                                                 int groups, int nlevels,
                                                                 unsigned long long *s1,
                                                                 unsigned long long *s2,
-                                                                unsigned long long *keys) {
+                                                                unsigned long long *keys,
+                                                                uint32_t one) {
     const int lane = threadIdx.x & 31;
     const int row = blockIdx.x / groups;
     const int64_t s0 =
@@ -185,9 +213,9 @@ __global__ void __launch_bounds__(32 * kWarps, 3) detect_kernel(const float *__r
         return;
     const float *x = plane + (int64_t)row * pitch;
     if (s0 + 32 * kKH <= nsamp)
-        detect_segment<INT, false>(x, nsamp, s0, row, nlevels, lane, s1, s2, keys);
+        detect_segment<INT, false>(x, nsamp, s0, row, nlevels, lane, one, s1, s2, keys);
     else
-        detect_segment<INT, true>(x, nsamp, s0, row, nlevels, lane, s1, s2, keys);
+        detect_segment<INT, true>(x, nsamp, s0, row, nlevels, lane, one, s1, s2, keys);
 }
 
 // One thread per row: sums and keys -> mean, std, S/N, t (in place).
@@ -275,10 +303,10 @@ extern "C" dd_status dd_detect(const float *plane, int64_t pitch, int ndm, int64
     auto *keys = reinterpret_cast<unsigned long long *>(snr);
     if (integer_valued)
         detect_kernel<true><<<grid, 32 * kWarps, 0, s>>>(plane, pitch, nsamp, (int)groups, nlevels,
-                                                         s1, s2, keys);
+                                                         s1, s2, keys, 1u);
     else
         detect_kernel<false><<<grid, 32 * kWarps, 0, s>>>(plane, pitch, nsamp, (int)groups,
-                                                          nlevels, s1, s2, keys);
+                                                          nlevels, s1, s2, keys, 1u);
     e = cudaGetLastError();
     if (e == cudaSuccess) {
         const unsigned fg = (unsigned)((ndm + 255) / 256);
