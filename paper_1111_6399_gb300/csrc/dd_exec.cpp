@@ -127,7 +127,26 @@ extern "C" dd_status dd_execute_host(dd_plan_t p, const void *in_host, dd_dtype 
 
     const int64_t elem = dd::elem_size(dtype);
     const int64_t S = p->maxshift;
-    const int64_t B = std::min<int64_t>(nsamp_out, std::max<int64_t>(65536, 2 * S));
+    // Output blocks: short first and last blocks (the first block's input
+    // copy and the last block's output copy overlap no kernel), long middle
+    // blocks (each output copy overlaps the next block's kernel).
+    std::vector<int64_t> blocks;
+    {
+        const int64_t mid = std::max<int64_t>(49152, 2 * S);
+        const int64_t edge = std::min<int64_t>(16384, std::max<int64_t>(4096, nsamp_out / 8));
+        if (nsamp_out <= 2 * edge + mid / 2) {
+            for (int64_t t = 0; t < nsamp_out; t += mid)
+                blocks.push_back(std::min(mid, nsamp_out - t));
+        } else {
+            const int64_t rest = nsamp_out - 2 * edge;
+            const int64_t m = (rest + mid - 1) / mid;
+            blocks.push_back(edge);
+            for (int64_t j = 0; j < m; ++j)
+                blocks.push_back(rest / m + (j < rest % m ? 1 : 0));
+            blocks.push_back(edge);
+        }
+    }
+    const int64_t B = *std::max_element(blocks.begin(), blocks.end());
     const int64_t dpitch_in = ((B + S) * elem + 15) / 16 * 16;   // bytes
     const int64_t dpitch_out = (B + 3) / 4 * 4;                 // floats
     const size_t need_in = (size_t)dpitch_in * p->nchan;
@@ -160,12 +179,12 @@ extern "C" dd_status dd_execute_host(dd_plan_t p, const void *in_host, dd_dtype 
     }
     const uint8_t *src = static_cast<const uint8_t *>(in_host);
     const int64_t hpitch_in = in_pitch * elem;
-    const int64_t nblk = (nsamp_out + B - 1) / B;
-    for (int64_t k = 0; k < nblk; ++k) {
+    const int64_t nblk = (int64_t)blocks.size();
+    int64_t t0 = 0, prev_nb = 0;
+    for (int64_t k = 0; k < nblk; t0 += blocks[k], prev_nb = blocks[k], ++k) {
         const int i = (int)(k & 1);
         cudaStream_t s = ws.s[i];
-        const int64_t t0 = k * B;
-        const int64_t nb = std::min(B, nsamp_out - t0);
+        const int64_t nb = blocks[k];
         uint8_t *din = static_cast<uint8_t *>(ws.in[i]);
         cudaError_t e = cudaSuccess;
         if (k >= 2)  // the block after the previous user of this slot read its tail
@@ -177,8 +196,9 @@ extern "C" dd_status dd_execute_host(dd_plan_t p, const void *in_host, dd_dtype 
             e = cudaStreamWaitEvent(s, ws.landed[1 - i], 0);
             if (e == cudaSuccess)
                 e = cudaMemcpy2DAsync(din, dpitch_in,
-                                      static_cast<uint8_t *>(ws.in[1 - i]) + B * elem, dpitch_in,
-                                      (size_t)(S * elem), p->nchan, cudaMemcpyDeviceToDevice, s);
+                                      static_cast<uint8_t *>(ws.in[1 - i]) + prev_nb * elem,
+                                      dpitch_in, (size_t)(S * elem), p->nchan,
+                                      cudaMemcpyDeviceToDevice, s);
             if (e == cudaSuccess)
                 e = cudaEventRecord(ws.tail_read[1 - i], s);
             if (e == cudaSuccess)

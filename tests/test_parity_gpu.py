@@ -186,6 +186,28 @@ def test_execute_host_matches_device_path(dd, oracle_lib):
     assert np.array_equal(out[d_idx, t_idx].astype(np.float64), want)
 
 
+def test_execute_host_with_tails_longer_than_a_block(dd, oracle_lib):
+    """Host-buffer blocks are uneven (short first and last blocks); here maxshift
+    (about 32400 samples) exceeds the 12500-sample edge blocks, so every overlap
+    tail spans more than one block of input."""
+    rng = np.random.default_rng(9)
+    nchan = 64
+    dms = np.linspace(0.0, 2000.0, 40).astype(np.float32)
+    plan = dd.Plan(nchan, 1500.0, -300.0 / nchan, 64e-6, dms)
+    assert plan.maxshift > 30000
+    nsamp_out = 100_000
+    nin = nsamp_out + plan.maxshift
+    data = fb.random_filterbank(rng, nchan, nin, "u8")
+    dev = _run(dd, plan, np.pad(data, ((0, 0), (0, (-nin) % 16))), nin, nsamp_out)
+    out = np.full((len(dms), nsamp_out), -1.0, np.float32)
+    plan.execute_host(data, out)
+    assert np.array_equal(out, dev)
+    table = oracle_lib.dmshift(nchan, 1500.0, -300.0 / nchan, 64e-6)
+    d_idx, t_idx = sample_cells(rng, len(dms), nsamp_out, 300)
+    want, _ = oracle_lib.dedisperse_cells(data, table, dms, d_idx, t_idx)
+    assert np.array_equal(out[d_idx, t_idx].astype(np.float64), want)
+
+
 def test_lband_full_size_sampled_cells(dd, oracle_lib):
     """The 1024-channel L-band beam at full size, default tiles (the benchmarked
     launch): sampled cells bit-exact, DM-0 row equal to the channel sum, and
