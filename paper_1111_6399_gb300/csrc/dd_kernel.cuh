@@ -737,8 +737,8 @@ __global__ void __launch_bounds__(32 * (max_consumer_warps(DT, NW) + 1 + (ELEM <
         const bool cross = !last && !widen;
         const int bn = (int)((g + 1) % nst);
         const int *tbn = atab + bn * tab_stride + 2 * kw;
-        // Unrolled by two pairs: measured 2 % faster (L-band, (4,12,1,8,8)) than
-        // the plain loop, which moves the rolling buffer at every back-edge.
+        // Unrolled by two pairs: measured 2 % faster than the plain loop on
+        // the L-band beam at (4,12,1,8,8); unrolling by 4 measured slower.
 #pragma unroll 2
         for (int q = 0; q < q_plain; ++q) {
 #pragma unroll
