@@ -48,8 +48,8 @@ ADD_LANES_PER_SM = 128  # FP32/INT32 lanes per SM per clock
 # dtype and tile shape; any other run reports traffic null.
 PROFILED_TRAFFIC = [
     {"workload": "lband-1024ch-1024dm-131072", "dtype": "u8", "tiles": [4, 12, 1, 8, 8],
-     "kernel_sha256": "bbb320f94891bc8e26f584efa6df2a383557ca8287901e441875502a47c35220",
-     "bytes": 152856064 + 520188160, "source": "profiles/dedisperse_lband_u8_full.md"},
+     "kernel_sha256": "de4282c324bdf36a83c1fe1cc46f999ae07ee69b3da4a6f5babc261a6b9e5045",
+     "bytes": 151974656 + 520219904, "source": "profiles/dedisperse_lband_u8_full.md"},
 ]
 
 
