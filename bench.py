@@ -405,6 +405,7 @@ def serving_section(dd, torch, dev, seconds: float = 8.0, speed: float = 1.25):
             "mean_batch": st_rt["mean_batch"], "slots": st_rt["slots"],
             "device_bytes": st_rt["device_bytes"],
             "saturated_blocks_per_s": sat_blocks / wall_sat,
+            "saturated_mean_batch": sat_blocks / max(1, st["batches"] - st_rt["batches"]),
             "saturated_adds_per_s": sat_blocks * adds_block / wall_sat,
             "real_time_beams_sustained": sat_blocks / wall_sat * block_s,
             "wall_s": wall_rt + wall_sat}
