@@ -84,6 +84,9 @@ def _lib(omp: bool = False) -> ctypes.CDLL:
             lib.oracle_detect.argtypes = [p, ctypes.c_int, i64, i64, ctypes.c_int, ctypes.c_int,
                                           p, p, p, p]
             lib.oracle_detect.restype = None
+            lib.oracle_frontend.argtypes = [p, i64, ctypes.c_int, i64, ctypes.c_int,
+                                            ctypes.c_double, p, i64, p, p]
+            lib.oracle_frontend.restype = None
             _LIBS[omp] = lib
         return _LIBS[omp]
 
@@ -226,3 +229,21 @@ def detect(plane: np.ndarray, nlevels: int, integer_valued: bool):
     _lib().oracle_detect(_ptr(x), ndm, nsamp, nsamp, nlevels, int(bool(integer_valued)),
                          _ptr(mean), _ptr(std), _ptr(snr), _ptr(tpk))
     return mean, std, snr, tpk
+
+
+def frontend(volts: np.ndarray, nint: int, k_clip: float):
+    """Stokes I, integration over nint raw samples, RFI clipping above
+    mean + k_clip*std and quantisation to uint8 (rules in the C file).
+    volts: int8 [nchan][nsamp_raw][4] (Xre, Xim, Yre, Yim).  Returns
+    (out uint8 [nchan][nsamp_raw // nint], mean[nchan], std[nchan])."""
+    v = np.ascontiguousarray(volts, dtype=np.int8)
+    if v.ndim != 3 or v.shape[2] != 4 or nint < 1:
+        raise ValueError("volts must be int8 [nchan][nsamp_raw][4] and nint >= 1")
+    nchan, nraw = v.shape[0], v.shape[1]
+    n = nraw // nint
+    out = np.empty((nchan, n), dtype=np.uint8)
+    mean = np.empty(nchan, dtype=np.float64)
+    std = np.empty(nchan, dtype=np.float64)
+    _lib().oracle_frontend(_ptr(v), 4 * nraw, nchan, nraw, nint, float(k_clip), _ptr(out), n,
+                           _ptr(mean), _ptr(std))
+    return out, mean, std

@@ -300,3 +300,68 @@ void oracle_detect(const double *plane, int ndm, int64_t pitch, int64_t nsamp, i
         }
     }
 }
+
+/*
+ * Front end: dual-polarisation voltages -> the uint8 filterbank the
+ * de-dispersion reads.  The paper's pipeline generates Stokes parameters,
+ * excises RFI and integrates before the dispersion search (Sec. 1); it gives
+ * no formulas, so the steps are:
+ *
+ *   volts[c][i] = four int8 values (Xre, Xim, Yre, Yim) of raw sample i of
+ *   channel c (rows of `pitch` bytes);
+ *   Stokes I of a raw sample: Xre^2 + Xim^2 + Yre^2 + Yim^2;
+ *   P[c][t] = sum of Stokes I over raw samples t*nint .. t*nint + nint - 1,
+ *   t = 0 .. nsamp_raw/nint - 1 (an exact integer);
+ *   per channel, over t: mean = S1/n, std = sqrt(S2/n - mean^2) (0 if
+ *   negative), S1 = sum P, S2 = sum P^2 exact, then FP64;
+ *   RFI excision: P > floor(mean + k*std) (k = k_clip, FP64) is replaced by
+ *   mean (the code becomes 128);
+ *   quantisation: m = (float)mean, s = (float)(16.0 / std),
+ *   code = clamp(rint(128 + ((float)P - m) * s), 0, 255) in FP32, one IEEE
+ *   operation at a time (round half to even); std == 0 gives 128 everywhere.
+ *
+ * Outputs mean and std per channel (FP64) and out[c][t] (uint8).
+ */
+void oracle_frontend(const int8_t *volts, int64_t pitch, int nchan, int64_t nsamp_raw, int nint,
+                     double k_clip, uint8_t *out, int64_t out_pitch, double *mean_out,
+                     double *std_out)
+{
+    const int64_t n = nsamp_raw / nint;
+    int64_t *p = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
+    for (int c = 0; c < nchan; ++c) {
+        const int8_t *row = volts + (int64_t)c * pitch;
+        uint64_t s1 = 0, s2 = 0;
+        for (int64_t t = 0; t < n; ++t) {
+            int64_t acc = 0;
+            for (int j = 0; j < nint; ++j) {
+                const int8_t *v = row + 4 * (t * nint + j);
+                acc += (int64_t)v[0] * v[0] + (int64_t)v[1] * v[1] + (int64_t)v[2] * v[2] +
+                       (int64_t)v[3] * v[3];
+            }
+            p[t] = acc;
+            s1 += (uint64_t)acc;
+            s2 += (uint64_t)acc * (uint64_t)acc;
+        }
+        const double dn = (double)n;
+        const double mean = n > 0 ? (double)s1 / dn : 0.0;
+        double var = n > 0 ? (double)s2 / dn - mean * mean : 0.0;
+        if (var < 0.0)
+            var = 0.0;
+        const double sd = sqrt(var);
+        mean_out[c] = mean;
+        std_out[c] = sd;
+        const int64_t thr = (int64_t)floor(mean + k_clip * sd);
+        const float m = (float)mean;
+        const float s = sd > 0.0 ? (float)(16.0 / sd) : 0.0f;
+        for (int64_t t = 0; t < n; ++t) {
+            uint8_t code = 128;
+            if (sd > 0.0 && p[t] <= thr) {
+                const float d = (float)p[t] - m;
+                const float v = rintf(128.0f + d * s);
+                code = (uint8_t)(v < 0.0f ? 0.0f : (v > 255.0f ? 255.0f : v));
+            }
+            out[(int64_t)c * out_pitch + t] = code;
+        }
+    }
+    free(p);
+}
