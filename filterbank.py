@@ -65,7 +65,7 @@ def dm_grid(dm_lo: float, dm_step: float, ndm: int) -> np.ndarray:
     return (float(dm_lo) + np.arange(ndm, dtype=np.float64) * float(dm_step)).astype(np.float32)
 
 
-# The five workloads of the build, by what they are.
+# The workloads, by what they are.
 SMALL = Workload("small-64ch-64dm-8k", nchan=64, fch1=1500.0, foff=-1.0, tsamp=64e-6,
                  nsamp_out=8192, ndm=64, dm_lo=0.0, dm_step=1.0, seed=1,
                  pulses=(Pulse(30.0, 2000, 4, 40.0),))
@@ -234,3 +234,93 @@ def add_pulse_u8(data: np.ndarray, delays: np.ndarray, pulse: Pulse, nsamp: int)
         if lo < hi:
             seg = data[c, lo:hi].astype(np.int32) + int(pulse.amp)
             data[c, lo:hi] = np.minimum(seg, 255).astype(np.uint8)
+
+
+# ---------------------------------------------------------------------------
+# Dual-polarisation voltages for the front end (Stokes I, integration, RFI
+# clipping, quantisation).  Each raw sample is four int8 values (Xre, Xim,
+# Yre, Yim).  Recipe:
+#   * four seeded pools (PCG64(seed)) of N(0, sigma) components, sigma in
+#     (8, 12, 18, 27), rounded half to even and clipped to [-128, 127]; channel
+#     c takes pool which[c] (a stand-in for the bandpass) from raw-sample
+#     offset offs[c] (both drawn from PCG64(seed + 1));
+#   * RFI: narrowband tones -- about one channel in 64 holds (100, 0, 100, 0)
+#     over a seeded range of 0.5..4 % of its samples -- and two broadband
+#     impulses, every channel (50, 50, 50, 50) over a seeded range of 0.1 % of
+#     the samples.
+# The paper names the steps of its front end but not its signal levels; these
+# put the RFI far above mean + 4 std of the integrated power.
+# ---------------------------------------------------------------------------
+
+VOLT_SIGMAS = (8.0, 12.0, 18.0, 27.0)
+
+
+@dataclass(frozen=True)
+class VoltageLayout:
+    nchan: int
+    nraw: int
+    which: np.ndarray      # pool index per channel
+    offs: np.ndarray       # raw-sample offset into the pool per channel
+    tones: tuple           # (channel, r0, r1)
+    impulses: tuple        # (r0, r1), all channels
+
+
+class VoltagePool:
+    def __init__(self, seed: int, size: int = 1 << 22):
+        rng = np.random.Generator(np.random.PCG64(seed))
+        self.seed = seed
+        self.size = size
+        self.pools = np.stack([
+            np.clip(np.rint(rng.normal(0.0, s, size=(size, 4))), -128, 127).astype(np.int8)
+            for s in VOLT_SIGMAS])
+
+    def layout(self, nchan: int, nraw: int, rfi: bool = True) -> VoltageLayout:
+        if nraw > self.size:
+            raise ValueError("rows longer than the voltage pool")
+        rng = np.random.Generator(np.random.PCG64(self.seed + 1))
+        which = rng.integers(0, len(VOLT_SIGMAS), size=nchan)
+        offs = rng.integers(0, self.size - nraw + 1, size=nchan)
+        tones, impulses = [], []
+        if rfi and nraw > 0:
+            for c in rng.choice(nchan, size=max(1, nchan // 64), replace=False):
+                ln = max(1, int(nraw * rng.uniform(0.005, 0.04)))
+                r0 = int(rng.integers(0, nraw - ln + 1))
+                tones.append((int(c), r0, r0 + ln))
+            for _ in range(2):
+                ln = max(1, nraw // 1000)
+                r0 = int(rng.integers(0, nraw - ln + 1))
+                impulses.append((r0, r0 + ln))
+        return VoltageLayout(nchan, nraw, which, offs, tuple(tones), tuple(impulses))
+
+    def rows(self, lay: VoltageLayout, chans=None) -> np.ndarray:
+        """int8 [len(chans)][nraw][4] on the host (all channels by default)."""
+        chans = range(lay.nchan) if chans is None else chans
+        out = np.empty((len(chans), lay.nraw, 4), dtype=np.int8)
+        for i, c in enumerate(chans):
+            o = int(lay.offs[c])
+            out[i] = self.pools[lay.which[c], o:o + lay.nraw]
+            for tc, r0, r1 in lay.tones:
+                if tc == c:
+                    out[i, r0:r1] = (100, 0, 100, 0)
+            for r0, r1 in lay.impulses:
+                out[i, r0:r1] = (50, 50, 50, 50)
+        return out
+
+    def rows_torch(self, lay: VoltageLayout, device, pitch_bytes: int | None = None):
+        """The same rows built on a torch device (copies and fills only):
+        an int8 tensor [nchan][pitch_bytes] whose first 4*nraw bytes of row c
+        are rows(lay)[c]; returned with the [nchan][nraw][4] view."""
+        import torch
+        pitch = 4 * lay.nraw if pitch_bytes is None else pitch_bytes
+        buf = torch.zeros((lay.nchan, pitch), dtype=torch.int8, device=device)
+        pools = torch.from_numpy(self.pools.reshape(len(VOLT_SIGMAS), -1)).to(device)
+        for c in range(lay.nchan):
+            o = 4 * int(lay.offs[c])
+            buf[c, :4 * lay.nraw] = pools[int(lay.which[c]), o:o + 4 * lay.nraw]
+        view = buf[:, :4 * lay.nraw].unflatten(1, (lay.nraw, 4))
+        tone = torch.tensor([100, 0, 100, 0], dtype=torch.int8, device=device)
+        for c, r0, r1 in lay.tones:
+            view[c, r0:r1] = tone
+        for r0, r1 in lay.impulses:
+            view[:, r0:r1] = 50
+        return buf, view

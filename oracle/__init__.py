@@ -85,7 +85,7 @@ def _lib(omp: bool = False) -> ctypes.CDLL:
                                           p, p, p, p]
             lib.oracle_detect.restype = None
             lib.oracle_frontend.argtypes = [p, i64, ctypes.c_int, i64, ctypes.c_int,
-                                            ctypes.c_double, p, i64, p, p]
+                                            ctypes.c_double, ctypes.c_int, p, i64, p, p]
             lib.oracle_frontend.restype = None
             _LIBS[omp] = lib
         return _LIBS[omp]
@@ -231,19 +231,20 @@ def detect(plane: np.ndarray, nlevels: int, integer_valued: bool):
     return mean, std, snr, tpk
 
 
-def frontend(volts: np.ndarray, nint: int, k_clip: float):
-    """Stokes I, integration over nint raw samples, RFI clipping above
-    mean + k_clip*std and quantisation to uint8 (rules in the C file).
-    volts: int8 [nchan][nsamp_raw][4] (Xre, Xim, Yre, Yim).  Returns
-    (out uint8 [nchan][nsamp_raw // nint], mean[nchan], std[nchan])."""
+def frontend(volts: np.ndarray, nint: int, k_clip: float, niter: int = 1):
+    """Stokes I, integration over nint raw samples, RFI excision by niter
+    passes of sigma clipping at mean + k_clip*std, and quantisation to uint8
+    (rules in the C file).  volts: int8 [nchan][nsamp_raw][4] (Xre, Xim, Yre,
+    Yim).  Returns (out uint8 [nchan][nsamp_raw // nint], mean[nchan],
+    std[nchan]), mean and std those of the last pass."""
     v = np.ascontiguousarray(volts, dtype=np.int8)
-    if v.ndim != 3 or v.shape[2] != 4 or nint < 1:
-        raise ValueError("volts must be int8 [nchan][nsamp_raw][4] and nint >= 1")
+    if v.ndim != 3 or v.shape[2] != 4 or nint < 1 or niter < 1:
+        raise ValueError("volts must be int8 [nchan][nsamp_raw][4], nint >= 1, niter >= 1")
     nchan, nraw = v.shape[0], v.shape[1]
     n = nraw // nint
     out = np.empty((nchan, n), dtype=np.uint8)
     mean = np.empty(nchan, dtype=np.float64)
     std = np.empty(nchan, dtype=np.float64)
-    _lib().oracle_frontend(_ptr(v), 4 * nraw, nchan, nraw, nint, float(k_clip), _ptr(out), n,
-                           _ptr(mean), _ptr(std))
+    _lib().oracle_frontend(_ptr(v), 4 * nraw, nchan, nraw, nint, float(k_clip), int(niter),
+                           _ptr(out), n, _ptr(mean), _ptr(std))
     return out, mean, std

@@ -312,25 +312,26 @@ void oracle_detect(const double *plane, int ndm, int64_t pitch, int64_t nsamp, i
  *   Stokes I of a raw sample: Xre^2 + Xim^2 + Yre^2 + Yim^2;
  *   P[c][t] = sum of Stokes I over raw samples t*nint .. t*nint + nint - 1,
  *   t = 0 .. nsamp_raw/nint - 1 (an exact integer);
- *   per channel, over t: mean = S1/n, std = sqrt(S2/n - mean^2) (0 if
- *   negative), S1 = sum P, S2 = sum P^2 exact, then FP64;
- *   RFI excision: P > floor(mean + k*std) (k = k_clip, FP64) is replaced by
- *   mean (the code becomes 128);
- *   quantisation: m = (float)mean, s = (float)(16.0 / std),
+ *   RFI excision by iterated sigma clipping, per channel: the kept set starts
+ *   as every t; each of niter passes takes, over the kept set, cnt, S1 = sum P
+ *   and S2 = sum P^2 (exact), then mean = S1/cnt, std = sqrt(S2/cnt - mean^2)
+ *   (0 if negative; both 0 if cnt == 0) and thr = floor(mean + k*std) (FP64,
+ *   k = k_clip), and the next kept set is {t : P[t] <= thr};
+ *   with the last pass's mean, std and thr: P > thr is replaced by the mean
+ *   (code 128); otherwise m = (float)mean, s = (float)(16.0 / std),
  *   code = clamp(rint(128 + ((float)P - m) * s), 0, 255) in FP32, one IEEE
  *   operation at a time (round half to even); std == 0 gives 128 everywhere.
  *
- * Outputs mean and std per channel (FP64) and out[c][t] (uint8).
+ * Outputs the last pass's mean and std per channel (FP64) and out[c][t].
  */
 void oracle_frontend(const int8_t *volts, int64_t pitch, int nchan, int64_t nsamp_raw, int nint,
-                     double k_clip, uint8_t *out, int64_t out_pitch, double *mean_out,
+                     double k_clip, int niter, uint8_t *out, int64_t out_pitch, double *mean_out,
                      double *std_out)
 {
     const int64_t n = nsamp_raw / nint;
     int64_t *p = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
     for (int c = 0; c < nchan; ++c) {
         const int8_t *row = volts + (int64_t)c * pitch;
-        uint64_t s1 = 0, s2 = 0;
         for (int64_t t = 0; t < n; ++t) {
             int64_t acc = 0;
             for (int j = 0; j < nint; ++j) {
@@ -339,18 +340,31 @@ void oracle_frontend(const int8_t *volts, int64_t pitch, int nchan, int64_t nsam
                        (int64_t)v[3] * v[3];
             }
             p[t] = acc;
-            s1 += (uint64_t)acc;
-            s2 += (uint64_t)acc * (uint64_t)acc;
         }
-        const double dn = (double)n;
-        const double mean = n > 0 ? (double)s1 / dn : 0.0;
-        double var = n > 0 ? (double)s2 / dn - mean * mean : 0.0;
-        if (var < 0.0)
-            var = 0.0;
-        const double sd = sqrt(var);
+        int64_t thr = INT64_MAX;
+        double mean = 0.0, sd = 0.0;
+        for (int it = 0; it < niter; ++it) {
+            uint64_t cnt = 0, s1 = 0, s2 = 0;
+            for (int64_t t = 0; t < n; ++t) {
+                if (p[t] <= thr) {
+                    cnt += 1;
+                    s1 += (uint64_t)p[t];
+                    s2 += (uint64_t)p[t] * (uint64_t)p[t];
+                }
+            }
+            mean = 0.0;
+            double var = 0.0;
+            if (cnt > 0) {
+                mean = (double)s1 / (double)cnt;
+                var = (double)s2 / (double)cnt - mean * mean;
+            }
+            if (var < 0.0)
+                var = 0.0;
+            sd = sqrt(var);
+            thr = (int64_t)floor(mean + k_clip * sd);
+        }
         mean_out[c] = mean;
         std_out[c] = sd;
-        const int64_t thr = (int64_t)floor(mean + k_clip * sd);
         const float m = (float)mean;
         const float s = sd > 0.0 ? (float)(16.0 / sd) : 0.0f;
         for (int64_t t = 0; t < n; ++t) {
