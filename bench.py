@@ -289,6 +289,53 @@ def unpack_section(dd, torch, dev, w: fb.Workload, nin: int, hbm_gbs: float, rep
     return res
 
 
+def frontend_section(dd, torch, dev, w: fb.Workload, nin: int, hbm_gbs: float, nint: int = 16,
+                     niter: int = 3, k_clip: float = 4.0, reps: int = 10, nchan: int = 0):
+    """dd_frontend producing the beam's uint8 input block (w.nchan channels x
+    nin spectra) from nint raw dual-polarisation samples per spectrum, with
+    niter clipping passes: HBM-bound.  'compulsory' bytes are the voltages
+    read and the codes written; 'moved' adds the integrated powers written
+    once and read niter times.  Voltages (several GB) exceed L2.  nchan > 0
+    takes only the first nchan channels (a smaller case for profiling)."""
+    nchan = w.nchan if nchan <= 0 else min(nchan, w.nchan)
+    pool = fb.VoltagePool(23)
+    lay = pool.layout(nchan, nin * nint)
+    buf, v = pool.rows_torch(lay, dev)
+    pitch = (nin + 15) // 16 * 16
+    out = torch.empty((nchan, pitch), dtype=torch.uint8, device=dev)
+    work = torch.empty(dd.frontend_work_bytes(nchan, nin * nint, nint, niter),
+                       dtype=torch.uint8, device=dev)
+    for _ in range(3):
+        dd.frontend(v, nint, k_clip, niter, out=out, work=work)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    n0 = dd.launch_count()
+    e0.record()
+    for _ in range(reps):
+        _, mean, std = dd.frontend(v, nint, k_clip, niter, out=out, work=work)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    launches = (dd.launch_count() - n0) // reps
+    volts_b = nchan * nin * nint * 4
+    codes_b = nchan * nin
+    compulsory = volts_b + codes_b
+    moved = compulsory + nchan * nin * 4 * (1 + niter)
+    std_h = std.cpu().numpy()
+    res = {"workload": f"{nchan} channels x {nin} spectra x {nint} raw samples "
+                       f"(int8 Xre,Xim,Yre,Yim), {niter} clipping passes at {k_clip} sigma",
+           "bound": "hbm", "ms": ms, "peak_gbs": hbm_gbs, "launches": launches,
+           "compulsory_bytes": compulsory, "moved_bytes": moved,
+           "gbs": compulsory / ms / 1e6, "frac": compulsory / ms / 1e6 / hbm_gbs,
+           "moved_gbs": moved / ms / 1e6, "moved_frac": moved / ms / 1e6 / hbm_gbs,
+           "spectra_per_s": nin / (ms / 1e3),
+           "real_time_factor": (nin * w.tsamp) / (ms / 1e3),
+           "std_range": [float(std_h.min()), float(std_h.max())]}
+    del buf, v, out, work
+    torch.cuda.empty_cache()
+    return res
+
+
 def detect_section(dd, torch, out, w: fb.Workload, hbm_gbs: float, dms, reps: int = 20):
     """dd_detect (boxcar widths 1..256) on the beam's own (DM,t) plane: the
     plane (FP32, larger than L2) is read once per launch; bytes over
@@ -593,6 +640,9 @@ def run_ours(args, w):
         line["serving"] = serving_section(dd, torch, dev)
     if not args.no_unpack and world == 1:
         line["unpack"] = unpack_section(dd, torch, dev, w, nin, pk.get("hbm_gbs", 6800.0))
+    if not args.no_frontend and world == 1 and w.nchan * nin * 64 <= (24 << 30):
+        line["frontend"] = frontend_section(dd, torch, dev, w, nin, pk.get("hbm_gbs", 6800.0),
+                                            nchan=args.frontend_chans)
     if not args.no_cpu:
         line["cpu_baseline"] = cpu_oracle_sample(w)
     print(json.dumps(line), flush=True)
@@ -664,6 +714,10 @@ def main():
     ap.add_argument("--no-serve", action="store_true", help="skip the serving section")
     ap.add_argument("--no-unpack", action="store_true", help="skip the input unpacking section")
     ap.add_argument("--no-detect", action="store_true", help="skip the detection section")
+    ap.add_argument("--no-frontend", action="store_true",
+                    help="skip the voltage front-end section")
+    ap.add_argument("--frontend-chans", type=int, default=0,
+                    help="front-end section on the first N channels only (0: all)")
     ap.add_argument("--sweep", action="store_true",
                     help="run the Fig. 4 sweeps instead (one JSON line)")
     ap.add_argument("--tiles", default="", help="fixed tile shape dthr,dm_warps,time_warps,cstage")

@@ -232,6 +232,50 @@ dd_status dd_detect(const float *plane, int64_t pitch, int ndm, int64_t nsamp, i
                     int integer_valued, double *mean, double *std, double *snr, int64_t *t_peak,
                     void *stream);
 
+/* --- front end: voltages -> the uint8 filterbank -------------------------- */
+
+/* Turn channelised dual-polarisation voltages into the uint8 filterbank that
+ * dd_execute reads.  Sec. 1 of the paper lists the steps before the
+ * dispersion search (Stokes parameters, RFI excision, integration) without
+ * formulas; the library's reading:
+ *   I[c][r] = Xre^2 + Xim^2 + Yre^2 + Yim^2 of raw sample r (int8 each);
+ *   P[c][t] = I[c][t*nint] + ... + I[c][t*nint + nint - 1], t < n =
+ *   nsamp_raw / nint (trailing raw samples are dropped);
+ *   RFI excision by niter passes of sigma clipping: each pass takes, over
+ *   the samples the previous pass kept (all of them for the first), the
+ *   exact count, S1 = sum P and S2 = sum P^2, then mean = S1/cnt,
+ *   std = sqrt(S2/cnt - mean^2) (0 if negative; both 0 if cnt == 0) and
+ *   thr = floor(mean + k_clip*std) in FP64; the next pass keeps P <= thr;
+ *   with the last pass's values: P > thr becomes code 128, otherwise
+ *   code = clamp(rint(128 + ((float)P - (float)mean) * (float)(16/std)),
+ *   0, 255), in FP32 one IEEE operation at a time; std == 0 gives 128.
+ *   volts: device int8 [nchan][volts_pitch bytes], raw sample r of channel c
+ *          at bytes 4r..4r+3 of the row (Xre, Xim, Yre, Yim); 4-byte aligned,
+ *          volts_pitch >= 4*nsamp_raw and a multiple of 4 (16-byte aligned
+ *          rows with nint a multiple of 4 take 16-byte loads).
+ *   nint:  a power of two, 1..64; n <= 2^19 (the sums of P^2 stay exact).
+ *   k_clip: in (0, 1e9]; niter: 1..8 (1 is a single clip with the
+ *          statistics of all samples).
+ *   out:   device uint8 [nchan][out_pitch], 16-byte aligned, out_pitch >= n
+ *          and a multiple of 16; columns >= n are left untouched.
+ *   work:  device scratch of work_bytes >= dd_frontend_work_bytes(...),
+ *          16-byte aligned, owned by the caller (P and the exact sums; only
+ *          rows longer than the fused kernel holds use it).
+ *   mean, std: device double [nchan], 8-byte aligned: the last pass's values
+ *          (0 when n == 0).
+ * Rows of n <= 409600 run in one launch: a thread-block cluster of 1..8 CTAs
+ * per channel keeps P in shared memory, so the voltages are read once and
+ * nothing else touches HBM but the codes.  Longer rows keep P in work
+ * (niter + 1 launches and a memset).  Asynchronous on stream; bad arguments
+ * return DD_ERR_INVALID with nothing launched.  The oracle's front end gives
+ * the same codes, mean and std bit for bit. */
+dd_status dd_frontend(const void *volts, int64_t volts_pitch, int nchan, int64_t nsamp_raw,
+                      int nint, double k_clip, int niter, uint8_t *out, int64_t out_pitch,
+                      void *work, int64_t work_bytes, double *mean, double *std, void *stream);
+
+/* Bytes of work dd_frontend needs for this shape; -1 if the shape is invalid. */
+int64_t dd_frontend_work_bytes(int nchan, int64_t nsamp_raw, int nint, int niter);
+
 /* --- batches: uneven beams in one persistent launch ------------------------ */
 
 typedef struct dd_batch_s *dd_batch_t;

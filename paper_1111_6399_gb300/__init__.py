@@ -6,8 +6,9 @@ the library and raises ImportError if it has not been built
 (``python __graft_entry__.py``).
 """
 from ._binding import (DD_F16, DD_F32, DD_U8, Batch, DDError, Plan, Server, Tiles, check,
-                       dtype_code,
-                       detect, elem_size, launch_count, lib, profile_events, unpack, warp_span)
+                       detect, dtype_code, elem_size, frontend, frontend_work_bytes,
+                       launch_count, lib, profile_events, unpack, warp_span)
 
-__all__ = ["Plan", "Batch", "Server", "Tiles", "DDError", "DD_U8", "DD_F16", "DD_F32", "check", "dtype_code",
-           "elem_size", "warp_span", "launch_count", "profile_events", "unpack", "detect", "lib"]
+__all__ = ["Plan", "Batch", "Server", "Tiles", "DDError", "DD_U8", "DD_F16", "DD_F32", "check",
+           "dtype_code", "elem_size", "warp_span", "launch_count", "profile_events", "unpack",
+           "detect", "frontend", "frontend_work_bytes", "lib"]

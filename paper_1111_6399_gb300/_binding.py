@@ -31,6 +31,7 @@ EXPORTS = [
     "dd_batch_autotune", "dd_batch_sync", "dd_server_create", "dd_server_add_beam",
     "dd_submit", "dd_poll", "dd_server_drain", "dd_server_get_stats", "dd_server_destroy",
     "dd_selftest_wait_timeout", "dd_server_set_batch_window", "dd_unpack", "dd_detect",
+    "dd_frontend", "dd_frontend_work_bytes",
 ]
 
 
@@ -87,6 +88,9 @@ def _load() -> ctypes.CDLL:
         "dd_sync": (i32, [p, p]),
         "dd_unpack": (i32, [p, i32, i32, i64, p, i64, p]),
         "dd_detect": (i32, [p, i64, i32, i64, i32, i32, p, p, p, p, p]),
+        "dd_frontend": (i32, [p, i64, i32, i64, i32, ctypes.c_double, i32, p, i64, p, i64, p,
+                              p, p]),
+        "dd_frontend_work_bytes": (i64, [i32, i64, i32, i32]),
         "dd_profile_events": (None, [p, p]),
         "dd_autotune": (i32, [p, p, i32, i64, i64, p, i64, i64, p, i32,
                               ctypes.POINTER(TuneResult), i32, ctypes.POINTER(i32)]),
@@ -185,6 +189,49 @@ def detect(plane, nsamp: int | None = None, nlevels: int = 9, integer_valued: bo
                         ctypes.c_void_p(std.data_ptr()), ctypes.c_void_p(snr.data_ptr()),
                         ctypes.c_void_p(tpk.data_ptr()), ctypes.c_void_p(s.cuda_stream)))
     return mean, std, snr, tpk
+
+
+def frontend(volts, nint: int, k_clip: float, niter: int = 1, out=None, work=None,
+             stream=None):
+    """dd_frontend on an int8 CUDA tensor volts [nchan][nsamp_raw][4] (rows
+    contiguous): returns (out uint8 [nchan][pitch], mean[nchan], std[nchan]),
+    out's first nsamp_raw // nint columns the filterbank.  out may be given
+    (uint8, 2-D, contiguous rows, 16-byte aligned pitch); work may be given
+    (a CUDA uint8 tensor of at least frontend_work_bytes).  Asynchronous."""
+    import torch
+    if not volts.is_cuda or volts.dtype != torch.int8 or volts.dim() != 3 \
+            or volts.shape[2] != 4 or volts.stride(2) != 1 or volts.stride(1) != 4:
+        raise ValueError("volts must be an int8 CUDA tensor [nchan][nsamp_raw][4] with "
+                         "contiguous rows")
+    nchan, nraw = volts.shape[0], volts.shape[1]
+    n = nraw // int(nint) if int(nint) > 0 else 0
+    dev = volts.device
+    if out is None:
+        out = torch.empty((nchan, max(16, (n + 15) // 16 * 16)), dtype=torch.uint8, device=dev)
+    elif out.dtype != torch.uint8 or out.dim() != 2 or out.stride(1) != 1 or not out.is_cuda \
+            or out.shape[0] < nchan or out.shape[1] < n:
+        raise ValueError("out must be a 2-D uint8 CUDA tensor [>= nchan][>= n] with contiguous "
+                         "rows")
+    need = frontend_work_bytes(nchan, nraw, nint, niter)
+    if work is None:
+        work = torch.empty(max(need, 16), dtype=torch.uint8, device=dev)
+    mean = torch.empty(nchan, dtype=torch.float64, device=dev)
+    std = torch.empty(nchan, dtype=torch.float64, device=dev)
+    s = torch.cuda.current_stream(dev) if stream is None else stream
+    check(lib.dd_frontend(ctypes.c_void_p(volts.data_ptr()), volts.stride(0), nchan, nraw,
+                          int(nint), float(k_clip), int(niter), ctypes.c_void_p(out.data_ptr()),
+                          out.stride(0), ctypes.c_void_p(work.data_ptr()),
+                          work.numel() * work.element_size(), ctypes.c_void_p(mean.data_ptr()),
+                          ctypes.c_void_p(std.data_ptr()), ctypes.c_void_p(s.cuda_stream)))
+    return out, mean, std
+
+
+def frontend_work_bytes(nchan: int, nsamp_raw: int, nint: int, niter: int = 1) -> int:
+    """dd_frontend_work_bytes; raises DDError for an invalid shape."""
+    b = int(lib.dd_frontend_work_bytes(int(nchan), int(nsamp_raw), int(nint), int(niter)))
+    if b < 0:
+        raise DDError(-1, "invalid front-end shape (nchan, nsamp_raw, nint, niter)")
+    return b
 
 
 def profile_events(start=None, stop=None) -> None:

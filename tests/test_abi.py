@@ -164,6 +164,41 @@ def test_detect_validates_before_touching_a_gpu(dd):
     assert dd.lib.dd_detect(None, 10, 0, 10, 3, 1, None, None, None, None, None) == 0
 
 
+def test_frontend_validates_before_touching_a_gpu(dd):
+    """dd_frontend argument errors are DD_ERR_INVALID from host checks alone."""
+    P = 4096
+    need = dd.frontend_work_bytes(8, 1000, 4, 3)
+    assert need == 4 * 8 * 252 + 24 * 3 * 8          # P rows of 250 -> 252, 3 sum sets
+    good = dict(volts=P, vpitch=4000, nchan=8, nraw=1000, nint=4, k=4.0, niter=3, out=P,
+                opitch=256, work=P, wbytes=need, mean=P, std=P)
+    bad = [
+        dict(nint=3), dict(nint=0), dict(nint=128),     # powers of two up to 64
+        dict(niter=0), dict(niter=9),
+        dict(nchan=0), dict(nchan=65536),
+        dict(nraw=-1),
+        dict(nraw=(1 << 19) * 4 + 4, vpitch=16 * (1 << 21)),   # more than 2^19 outputs
+        dict(vpitch=3996),               # shorter than 4*nsamp_raw
+        dict(vpitch=4002),               # not a multiple of 4
+        dict(opitch=240),                # shorter than nsamp_raw / nint
+        dict(opitch=264),                # not a multiple of 16
+        dict(k=0.0), dict(k=-1.0), dict(k=2e9), dict(k=float("nan")),
+        dict(wbytes=need - 1),
+        dict(volts=0), dict(out=0), dict(work=0), dict(mean=0), dict(std=0),
+        dict(volts=P + 2), dict(out=P + 4), dict(work=P + 4), dict(mean=P + 4),
+    ]
+    for b in bad:
+        a = {**good, **b}
+        st = dd.lib.dd_frontend(ctypes.c_void_p(a["volts"]), a["vpitch"], a["nchan"], a["nraw"],
+                                a["nint"], a["k"], a["niter"], ctypes.c_void_p(a["out"]),
+                                a["opitch"], ctypes.c_void_p(a["work"]), a["wbytes"],
+                                ctypes.c_void_p(a["mean"]), ctypes.c_void_p(a["std"]), None)
+        assert st == -1, b
+    for shape in [(0, 1000, 4, 1), (8, 1000, 3, 1), (8, 1000, 4, 0), (8, 1 << 22, 4, 1)]:
+        assert dd.lib.dd_frontend_work_bytes(*shape) == -1, shape
+    with pytest.raises(dd.DDError):
+        dd.frontend_work_bytes(8, 1000, 4, 9)
+
+
 def test_status_codes_and_messages(dd):
     with pytest.raises(dd.DDError) as e:
         dd.Plan(8, 1500.0, -1.0, 0.0, [0.0])
