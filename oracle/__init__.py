@@ -87,6 +87,13 @@ def _lib(omp: bool = False) -> ctypes.CDLL:
             lib.oracle_frontend.argtypes = [p, i64, ctypes.c_int, i64, ctypes.c_int,
                                             ctypes.c_double, ctypes.c_int, p, i64, p, p]
             lib.oracle_frontend.restype = None
+            lib.oracle_pfb.argtypes = [p, i64, i64, ctypes.c_int, ctypes.c_int, p, ctypes.c_int,
+                                       p, p, p]
+            lib.oracle_pfb.restype = None
+            lib.oracle_pfb_quantise.argtypes = [p, i64, ctypes.c_double, p]
+            lib.oracle_pfb_quantise.restype = None
+            lib.oracle_pfb_prototype.argtypes = [ctypes.c_int, ctypes.c_int, p]
+            lib.oracle_pfb_prototype.restype = ctypes.c_int
             _LIBS[omp] = lib
         return _LIBS[omp]
 
@@ -248,3 +255,61 @@ def frontend(volts: np.ndarray, nint: int, k_clip: float, niter: int = 1):
     _lib().oracle_frontend(_ptr(v), 4 * nraw, nchan, nraw, nint, float(k_clip), int(niter),
                            _ptr(out), n, _ptr(mean), _ptr(std))
     return out, mean, std
+
+
+def pfb_nspec(nraw: int, M: int, T: int) -> int:
+    """Spectra of the channeliser: floor(nraw/M) - T + 1, or 0."""
+    return max(0, nraw // M - T + 1)
+
+
+def pfb(volts: np.ndarray, M: int, T: int, h: np.ndarray, spectra=None, threads: bool = False):
+    """Polyphase channeliser (definition in the C file), FP64.
+
+    volts: int8 [nsub][nraw][4] (Xre, Xim, Yre, Yim) subband voltages;
+    h: prototype filter, M*T values (taken as FP64).
+    spectra: None for every spectrum -> float64 [nsub*M][nspec][4] (row
+    s*M + c, channel c in increasing frequency); or a list of (s, n) ->
+    float64 [len][M][4].
+    """
+    v = np.ascontiguousarray(volts, dtype=np.int8)
+    if v.ndim != 3 or v.shape[2] != 4:
+        raise ValueError("volts must be int8 [nsub][nraw][4]")
+    h = np.ascontiguousarray(h, dtype=np.float64)
+    if M < 1 or T < 1 or h.size != M * T:
+        raise ValueError("h must hold M*T values")
+    nsub, nraw = v.shape[0], v.shape[1]
+    nspec = pfb_nspec(nraw, M, T)
+    full = spectra is None
+    if full:
+        sub = np.repeat(np.arange(nsub, dtype=np.int32), nspec)
+        spec = np.tile(np.arange(nspec, dtype=np.int64), nsub)
+    else:
+        sel = np.asarray(spectra, dtype=np.int64).reshape(-1, 2)
+        sub = np.ascontiguousarray(sel[:, 0], dtype=np.int32)
+        spec = np.ascontiguousarray(sel[:, 1], dtype=np.int64)
+        if len(sel) and (sub.min() < 0 or sub.max() >= nsub or spec.min() < 0
+                         or spec.max() >= nspec):
+            raise ValueError("spectrum outside the output")
+    out = np.empty((len(sub), M, 4), dtype=np.float64)
+    if len(sub):
+        _lib(threads).oracle_pfb(_ptr(v), 4 * nraw, nraw, M, T, _ptr(h), len(sub), _ptr(sub),
+                                 _ptr(spec), _ptr(out))
+    if full:
+        return out.reshape(nsub, nspec, M, 4).transpose(0, 2, 1, 3).reshape(nsub * M, nspec, 4)
+    return out
+
+
+def pfb_quantise(v: np.ndarray, scale: float) -> np.ndarray:
+    """int8 clamp(rint(v * scale), -127, 127) in FP64 (same shape as v)."""
+    x = np.ascontiguousarray(v, dtype=np.float64)
+    q = np.empty(x.shape, dtype=np.int8)
+    _lib().oracle_pfb_quantise(_ptr(x), x.size, float(scale), _ptr(q))
+    return q
+
+
+def pfb_prototype(M: int, T: int) -> np.ndarray:
+    """Hamming-windowed sinc prototype of M*T taps (FP64)."""
+    h = np.empty(M * T, dtype=np.float64)
+    if _lib().oracle_pfb_prototype(M, T, _ptr(h)) != 0:
+        raise ValueError("need M >= 1, T >= 1 and M*T >= 2")
+    return h

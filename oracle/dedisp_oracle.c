@@ -379,3 +379,100 @@ void oracle_frontend(const int8_t *volts, int64_t pitch, int nchan, int64_t nsam
     }
     free(p);
 }
+
+/*
+ * Polyphase channeliser: subband voltages -> finer frequency channels.  The
+ * paper's pipeline channelises the received subbands "in finer frequency"
+ * before it generates Stokes parameters (Sec. 1) and names the poly-phase
+ * filter (Sec. 5); it gives neither the filter nor the transform size, so the
+ * textbook critically sampled polyphase filter bank is used (a window of
+ * M*T samples weighted by a prototype low-pass filter, then an M-point DFT,
+ * advancing by M samples per spectrum):
+ *
+ *   volts[s][j] = four int8 (Xre, Xim, Yre, Yim) of raw sample j of subband s
+ *   (rows of `pitch` bytes); per polarisation x[j] = re + i*im;
+ *   M channels per subband, T taps, prototype h[m], m < M*T;
+ *   spectrum n, n = 0 .. floor(nraw/M) - T (none if floor(nraw/M) < T):
+ *       y_k[n] = sum_{m=0}^{M*T-1} h[m] * x[n*M + m] * exp(-2 pi i k m / M)
+ *   output channel c = (k + M/2) mod M of subband s (row s*M + c): the bins of
+ *   a subband in increasing frequency, the most negative bin (k = M/2) first.
+ *
+ * The sum is evaluated as written, term by term in FP64, with the phase
+ * exp(-2 pi i ((k*m) mod M) / M) taken from cos/sin in FP64.
+ * oracle_pfb computes the spectra (sub[i], spec[i]) of a list and writes, per
+ * listed spectrum, out[i][c][4] = (Xre, Xim, Yre, Yim) of every channel c.
+ */
+void oracle_pfb(const int8_t *volts, int64_t pitch, int64_t nraw, int M, int T, const double *h,
+                int nsel, const int *sub, const int64_t *spec, double *out)
+{
+    const double twopi = 6.283185307179586476925286766559;
+    double *cs = (double *)malloc(sizeof(double) * 2 * (size_t)M);
+    for (int r = 0; r < M; ++r) {
+        cs[2 * r] = cos(twopi * (double)r / (double)M);
+        cs[2 * r + 1] = sin(twopi * (double)r / (double)M);
+    }
+    const int64_t L = (int64_t)M * T;
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int i = 0; i < nsel; ++i) {
+        const int8_t *row = volts + (int64_t)sub[i] * pitch;
+        const int64_t n = spec[i];
+        for (int k = 0; k < M; ++k) {
+            double acc[4] = {0.0, 0.0, 0.0, 0.0};
+            for (int64_t m = 0; m < L; ++m) {
+                const int8_t *v = row + 4 * (n * M + m);
+                const int r = (int)(((int64_t)k * m) % M);
+                const double c = cs[2 * r], sn = -cs[2 * r + 1]; /* exp(-i theta) */
+                for (int pol = 0; pol < 2; ++pol) {
+                    const double re = h[m] * (double)v[2 * pol];
+                    const double im = h[m] * (double)v[2 * pol + 1];
+                    acc[2 * pol] += re * c - im * sn;
+                    acc[2 * pol + 1] += re * sn + im * c;
+                }
+            }
+            const int ch = (k + M / 2) % M;
+            for (int e = 0; e < 4; ++e)
+                out[((int64_t)i * M + ch) * 4 + e] = acc[e];
+        }
+    }
+    free(cs);
+}
+
+/*
+ * Requantisation of channelised voltages to int8 (so that the front end can
+ * read them): q = clamp(rint(v * scale), -127, 127), round half to even, in
+ * FP64.  The clip is symmetric so that negating a voltage negates its code.
+ */
+void oracle_pfb_quantise(const double *v, int64_t n, double scale, int8_t *q)
+{
+    for (int64_t i = 0; i < n; ++i) {
+        double u = rint(v[i] * scale);
+        if (u > 127.0)
+            u = 127.0;
+        if (u < -127.0)
+            u = -127.0;
+        q[i] = (int8_t)u;
+    }
+}
+
+/*
+ * Prototype filter of the channeliser, FP64: a Hamming-windowed sinc whose
+ * main lobe spans one channel (cutoff at half the channel spacing),
+ *     h[m] = sinc((m - (L-1)/2) / M) * (0.54 - 0.46 cos(2 pi m / (L-1))),
+ *     sinc(x) = sin(pi x) / (pi x), sinc(0) = 1, L = M*T (L > 1);
+ * unnormalised (its centre is near 1, its sum near M).  The paper names no
+ * filter; this is the common windowed-sinc design.
+ */
+int oracle_pfb_prototype(int M, int T, double *h)
+{
+    const int64_t L = (int64_t)M * T;
+    if (M < 1 || T < 1 || L < 2)
+        return -1;
+    const double pi = 3.141592653589793238462643383280;
+    for (int64_t m = 0; m < L; ++m) {
+        const double x = ((double)m - (double)(L - 1) / 2.0) / (double)M;
+        const double sinc = x == 0.0 ? 1.0 : sin(pi * x) / (pi * x);
+        const double w = 0.54 - 0.46 * cos(2.0 * pi * (double)m / (double)(L - 1));
+        h[m] = sinc * w;
+    }
+    return 0;
+}
