@@ -336,6 +336,58 @@ def frontend_section(dd, torch, dev, w: fb.Workload, nin: int, hbm_gbs: float, n
     return res
 
 
+def channeliser_section(dd, torch, dev, hbm_gbs: float, sm_mhz: float, nsub: int = 0,
+                        reps: int = 10) -> dict:
+    """dd_channelise (int8 output, the front end's element) on the two
+    channeliser workloads: 64 subbands x 16 channels and 4 subbands x 256
+    channels, 8 taps, the 1024 channels of the L-band front-end block.
+    Algorithmic bytes: the raw words read and the codes written; algorithmic
+    flops per spectrum and polarisation: 4*M*T for the FIR (a real tap times
+    a complex sample as two fused multiply-adds) and 5*M*log2(M) for the FFT.
+    The FP32 peak is 152 SMs x 128 lanes x 2 flops x the measured maximum
+    SM clock.  Inputs (9.7 GB) exceed L2.  nsub > 0 keeps the first nsub
+    subbands of each workload (a smaller case for profiling)."""
+    res = {"fp32_peak_tflops": SM_COUNT * ADD_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12,
+           "peak_gbs": hbm_gbs}
+    for w in (fb.CHANNELISER_LBAND, fb.CHANNELISER_WIDE):
+        ns = w.nsub if nsub <= 0 else min(nsub, w.nsub)
+        pool = fb.VoltagePool(w.seed)
+        v = pool.long_rows_torch(ns, w.nraw, dev)
+        h = torch.from_numpy(dd.pfb_prototype(w.M, w.T)).to(dev)
+        nspec = dd.channelise_nspec(w.nraw, w.M, w.T)
+        out = torch.empty((ns * w.M, (nspec + 3) // 4 * 4, 4), dtype=torch.int8, device=dev)
+        for _ in range(3):
+            dd.channelise(v, w.M, w.T, h, kind="ci8", scale=w.scale, out=out)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        n0 = dd.launch_count()
+        e0.record()
+        for _ in range(reps):
+            dd.channelise(v, w.M, w.T, h, kind="ci8", scale=w.scale, out=out)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        launches = (dd.launch_count() - n0) // reps
+        nbytes = 4 * ns * w.nraw + 4 * ns * w.M * nspec
+        flops = ns * nspec * 2 * (4 * w.M * w.T + 5 * w.M * math.log2(w.M))
+        gbs = nbytes / ms / 1e6
+        tflops = flops / ms / 1e9
+        t_hbm = nbytes / (hbm_gbs * 1e9)
+        t_fp = flops / (res["fp32_peak_tflops"] * 1e12)
+        res[w.name] = {
+            "workload": f"{ns} subbands x {w.M} channels x {w.T} taps, {nspec} spectra per "
+                        f"subband, int8 (Xre,Xim,Yre,Yim) in and out",
+            "ms": ms, "launches": launches, "bytes": nbytes, "gbs": gbs,
+            "hbm_frac": gbs / hbm_gbs, "flops": flops, "tflops": tflops,
+            "fp32_frac": tflops / res["fp32_peak_tflops"],
+            "bound": "hbm" if t_hbm >= t_fp else "fp32",
+            "roofline_frac": max(t_hbm, t_fp) / (ms / 1e3),
+            "raw_samples_per_s": ns * w.nraw / (ms / 1e3)}
+        del v, out
+        torch.cuda.empty_cache()
+    return res
+
+
 def detect_section(dd, torch, out, w: fb.Workload, hbm_gbs: float, dms, reps: int = 20):
     """dd_detect (boxcar widths 1..256) on the beam's own (DM,t) plane: the
     plane (FP32, larger than L2) is read once per launch; bytes over
@@ -643,6 +695,10 @@ def run_ours(args, w):
     if not args.no_frontend and world == 1 and w.nchan * nin * 64 <= (24 << 30):
         line["frontend"] = frontend_section(dd, torch, dev, w, nin, pk.get("hbm_gbs", 6800.0),
                                             nchan=args.frontend_chans)
+    if not args.no_pfb and world == 1:
+        line["channeliser"] = channeliser_section(dd, torch, dev, pk.get("hbm_gbs", 6800.0),
+                                                  pk.get("sm_max_mhz", 2070.0),
+                                                  nsub=args.pfb_subs)
     if not args.no_cpu:
         line["cpu_baseline"] = cpu_oracle_sample(w)
     print(json.dumps(line), flush=True)
@@ -718,6 +774,9 @@ def main():
                     help="skip the voltage front-end section")
     ap.add_argument("--frontend-chans", type=int, default=0,
                     help="front-end section on the first N channels only (0: all)")
+    ap.add_argument("--no-pfb", action="store_true", help="skip the channeliser section")
+    ap.add_argument("--pfb-subs", type=int, default=0,
+                    help="channeliser section on the first N subbands only (0: all)")
     ap.add_argument("--sweep", action="store_true",
                     help="run the Fig. 4 sweeps instead (one JSON line)")
     ap.add_argument("--tiles", default="", help="fixed tile shape dthr,dm_warps,time_warps,cstage")

@@ -324,3 +324,57 @@ class VoltagePool:
         for r0, r1 in lay.impulses:
             view[:, r0:r1] = 50
         return buf, view
+
+    def long_rows_torch(self, nrows: int, nraw: int, device, chunk: int = 1 << 21):
+        """int8 [nrows][nraw][4] on a torch device for rows longer than the
+        pool (copies only): row r takes pool which[r] and is filled chunk by
+        chunk from seeded pool offsets (PCG64(seed + 2)).  No RFI."""
+        import torch
+        rng = np.random.Generator(np.random.PCG64(self.seed + 2))
+        which = rng.integers(0, len(VOLT_SIGMAS), size=nrows)
+        chunk = min(chunk, self.size)
+        nchunk = (nraw + chunk - 1) // chunk
+        offs = rng.integers(0, self.size - chunk + 1, size=(nrows, max(nchunk, 1)))
+        pools = torch.from_numpy(self.pools).to(device)        # [4][size][4]
+        out = torch.empty((nrows, nraw, 4), dtype=torch.int8, device=device)
+        for r in range(nrows):
+            for k in range(nchunk):
+                a, b = k * chunk, min(nraw, (k + 1) * chunk)
+                o = int(offs[r, k])
+                out[r, a:b] = pools[int(which[r]), o:o + (b - a)]
+        return out
+
+
+# ---------------------------------------------------------------------------
+# Channeliser workloads (subband voltages for the polyphase filter bank).
+# Each subband row is int8 (Xre, Xim, Yre, Yim) noise from the voltage pools
+# above, filled chunk by chunk (VoltagePool.long_rows_torch).  The scale
+# brings a pool of sigma 18 to about 16 codes per component after the
+# prototype's gain (sqrt(sum h^2) is 3.8 for 16 x 8 taps, 15.2 for 256 x 8).
+# ---------------------------------------------------------------------------
+
+@dataclass(frozen=True)
+class ChanneliserWorkload:
+    name: str
+    nsub: int      # subbands (rows of raw samples)
+    M: int         # channels per subband
+    T: int         # taps per branch
+    nspec: int     # output spectra per subband
+    seed: int
+    scale: float   # int8 output: codes = rint(value * scale)
+
+    @property
+    def nraw(self) -> int:
+        return (self.nspec + self.T - 1) * self.M
+
+    def raw_bytes(self) -> int:
+        return 4 * self.nsub * self.nraw
+
+
+# 64 subbands x 16 channels = the 1024 channels of the L-band front-end block
+# (147628 output samples x 16 raw samples each per channel).
+CHANNELISER_LBAND = ChanneliserWorkload("pfb-64sub-16ch-8tap", nsub=64, M=16, T=8,
+                                        nspec=147628 * 16, seed=6, scale=0.25)
+# The same 1024 channels from 4 wide subbands of 256 channels.
+CHANNELISER_WIDE = ChanneliserWorkload("pfb-4sub-256ch-8tap", nsub=4, M=256, T=8,
+                                       nspec=147628 * 16, seed=7, scale=0.0625)

@@ -276,6 +276,61 @@ dd_status dd_frontend(const void *volts, int64_t volts_pitch, int nchan, int64_t
 /* Bytes of work dd_frontend needs for this shape; -1 if the shape is invalid. */
 int64_t dd_frontend_work_bytes(int nchan, int64_t nsamp_raw, int nint, int niter);
 
+/* --- channeliser: subband voltages -> finer channels ----------------------- */
+
+/* Output element kinds of dd_channelise. */
+enum {
+    DD_PFB_CF32 = 0,  /* four FP32 (Xre, Xim, Yre, Yim): 16 bytes per element   */
+    DD_PFB_CI8 = 1    /* four int8 codes (Xre, Xim, Yre, Yim): 4 bytes, the
+                         element dd_frontend reads                                */
+};
+
+/* Split each subband of dual-polarisation voltages into M finer channels with
+ * a critically sampled polyphase filter bank.  The paper channelises the
+ * received subbands in finer frequency before forming Stokes parameters
+ * (Sec. 1) and names the poly-phase filter (Sec. 5) without giving the
+ * filter or the transform size; the library's reading, per polarisation
+ * with x[j] = re + i*im of raw sample j:
+ *   y_k[n] = sum_{m < M*T} h[m] x[n*M + m] exp(-2 pi i k m / M),  k < M,
+ *   for spectra n < nspec = floor(nraw/M) - T + 1 (0 if negative);
+ *   channel c = (k + M/2) mod M of subband s goes to row s*M + c, so the
+ *   channels of a subband run in increasing frequency; column n.
+ *   volts: device int8 [nsub][volts_pitch bytes], raw sample j of subband s
+ *          at bytes 4j..4j+3 of the row (Xre, Xim, Yre, Yim); 4-byte aligned,
+ *          volts_pitch >= 4*nraw and a multiple of 4.
+ *   nchan_sub (M): 16, 32, 64, 128 or 256; ntaps (T): 1..16; nsub: 1..65535.
+ *   coeffs: device FP32 [M*T], the prototype filter h (dd_pfb_prototype
+ *          gives the windowed-sinc one); 4-byte aligned.
+ *   out_kind DD_PFB_CF32: FP32 elements, computed in FP32 (FIR by FMA, a
+ *          16 x M/16 four-step FFT with twiddles from sincospif); error
+ *          within (T + 6 log2 M + 8) * 2^-23 * sum_m |h[m]| |x| of the
+ *          exact value, |x| the sum of the component magnitudes.
+ *   out_kind DD_PFB_CI8: int8 codes q = clamp(rint(v * scale), -127, 127),
+ *          v the FP32 value above and v*scale rounded once to an integer
+ *          (ties to even); scale finite and > 0.  Cells whose exact value
+ *          lies within the FP32 error of a rounding boundary may take either
+ *          neighbouring code.
+ *   out:   device [nsub*M][out_pitch bytes], aligned to its element (4 or 16
+ *          bytes), out_pitch >= element * nspec and a multiple of it; columns
+ *          >= nspec are left untouched.
+ * One launch; each raw word is read from HBM once and each element written
+ * once.  Asynchronous on stream; bad arguments return DD_ERR_INVALID with
+ * nothing launched; nspec == 0 launches nothing. */
+dd_status dd_channelise(const void *volts, int64_t volts_pitch, int nsub, int64_t nraw,
+                        int nchan_sub, int ntaps, const float *coeffs, int out_kind, float scale,
+                        void *out, int64_t out_pitch, void *stream);
+
+/* Spectra dd_channelise produces per subband: floor(nraw/M) - T + 1, 0 if
+ * that is negative, -1 for an invalid M, T or nraw. */
+int64_t dd_channelise_nspec(int64_t nraw, int nchan_sub, int ntaps);
+
+/* Host: the windowed-sinc prototype of M*T taps, FP64 rounded once to FP32:
+ *   h[m] = sinc((m - (L-1)/2) / M) * (0.54 - 0.46 cos(2 pi m / (L-1))),
+ *   sinc(x) = sin(pi x)/(pi x), L = M*T >= 2 (a Hamming-windowed sinc whose
+ *   cutoff is half a channel spacing; its sum is about M).
+ * h: host float [M*T], owned by the caller.  The paper names no filter. */
+dd_status dd_pfb_prototype(int nchan_sub, int ntaps, float *h);
+
 /* --- batches: uneven beams in one persistent launch ------------------------ */
 
 typedef struct dd_batch_s *dd_batch_t;

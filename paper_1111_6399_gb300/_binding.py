@@ -31,7 +31,8 @@ EXPORTS = [
     "dd_batch_autotune", "dd_batch_sync", "dd_server_create", "dd_server_add_beam",
     "dd_submit", "dd_poll", "dd_server_drain", "dd_server_get_stats", "dd_server_destroy",
     "dd_selftest_wait_timeout", "dd_server_set_batch_window", "dd_unpack", "dd_detect",
-    "dd_frontend", "dd_frontend_work_bytes",
+    "dd_frontend", "dd_frontend_work_bytes", "dd_channelise", "dd_channelise_nspec",
+    "dd_pfb_prototype",
 ]
 
 
@@ -91,6 +92,9 @@ def _load() -> ctypes.CDLL:
         "dd_frontend": (i32, [p, i64, i32, i64, i32, ctypes.c_double, i32, p, i64, p, i64, p,
                               p, p]),
         "dd_frontend_work_bytes": (i64, [i32, i64, i32, i32]),
+        "dd_channelise": (i32, [p, i64, i32, i64, i32, i32, p, i32, ctypes.c_float, p, i64, p]),
+        "dd_channelise_nspec": (i64, [i64, i32, i32]),
+        "dd_pfb_prototype": (i32, [i32, i32, p]),
         "dd_profile_events": (None, [p, p]),
         "dd_autotune": (i32, [p, p, i32, i64, i64, p, i64, i64, p, i32,
                               ctypes.POINTER(TuneResult), i32, ctypes.POINTER(i32)]),
@@ -224,6 +228,61 @@ def frontend(volts, nint: int, k_clip: float, niter: int = 1, out=None, work=Non
                           work.numel() * work.element_size(), ctypes.c_void_p(mean.data_ptr()),
                           ctypes.c_void_p(std.data_ptr()), ctypes.c_void_p(s.cuda_stream)))
     return out, mean, std
+
+
+DD_PFB_CF32, DD_PFB_CI8 = 0, 1
+
+
+def channelise_nspec(nraw: int, nchan_sub: int, ntaps: int) -> int:
+    """dd_channelise_nspec; raises DDError for an invalid M, T or nraw."""
+    n = int(lib.dd_channelise_nspec(int(nraw), int(nchan_sub), int(ntaps)))
+    if n < 0:
+        raise DDError(-1, "invalid channeliser shape (nraw, nchan_sub, ntaps)")
+    return n
+
+
+def pfb_prototype(nchan_sub: int, ntaps: int):
+    """dd_pfb_prototype: the windowed-sinc prototype as a float32 numpy array."""
+    import numpy as np
+    h = np.empty(int(nchan_sub) * int(ntaps), dtype=np.float32)
+    check(lib.dd_pfb_prototype(int(nchan_sub), int(ntaps), ctypes.c_void_p(h.ctypes.data)))
+    return h
+
+
+def channelise(volts, nchan_sub: int, ntaps: int, coeffs, kind: str = "ci8",
+               scale: float = 1.0, out=None, stream=None):
+    """dd_channelise on an int8 CUDA tensor volts [nsub][nraw][4] (rows
+    contiguous) with float32 CUDA coeffs [nchan_sub*ntaps].  kind "ci8"
+    returns int8 [nsub*M][pitch][4] (the front end's element, pitch a
+    multiple of 4 spectra), "cf32" float32 [nsub*M][nspec][4]; the first
+    nspec columns hold the spectra.  out may be given with that layout.
+    Asynchronous."""
+    import torch
+    if not volts.is_cuda or volts.dtype != torch.int8 or volts.dim() != 3 \
+            or volts.shape[2] != 4 or volts.stride(2) != 1 or volts.stride(1) != 4:
+        raise ValueError("volts must be an int8 CUDA tensor [nsub][nraw][4] with contiguous "
+                         "rows")
+    if not coeffs.is_cuda or coeffs.dtype != torch.float32 or not coeffs.is_contiguous():
+        raise ValueError("coeffs must be a contiguous float32 CUDA tensor")
+    nsub, nraw = volts.shape[0], volts.shape[1]
+    M = int(nchan_sub)
+    nspec = channelise_nspec(nraw, M, ntaps)
+    code = {"ci8": DD_PFB_CI8, "cf32": DD_PFB_CF32}[kind]
+    dt = torch.int8 if code == DD_PFB_CI8 else torch.float32
+    dev = volts.device
+    if out is None:
+        cols = max(4, (nspec + 3) // 4 * 4) if code == DD_PFB_CI8 else max(1, nspec)
+        out = torch.empty((nsub * M, cols, 4), dtype=dt, device=dev)
+    elif out.dtype != dt or out.dim() != 3 or out.shape[2] != 4 or out.stride(2) != 1 \
+            or out.stride(1) != 4 or out.shape[0] < nsub * M or out.shape[1] < nspec:
+        raise ValueError("out must be a CUDA tensor [>= nsub*M][>= nspec][4] of the kind's "
+                         "dtype with contiguous rows")
+    s = torch.cuda.current_stream(dev) if stream is None else stream
+    check(lib.dd_channelise(ctypes.c_void_p(volts.data_ptr()), volts.stride(0), nsub, nraw, M,
+                            int(ntaps), ctypes.c_void_p(coeffs.data_ptr()), code, float(scale),
+                            ctypes.c_void_p(out.data_ptr()), out.stride(0) * out.element_size(),
+                            ctypes.c_void_p(s.cuda_stream)))
+    return out
 
 
 def frontend_work_bytes(nchan: int, nsamp_raw: int, nint: int, niter: int = 1) -> int:

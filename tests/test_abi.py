@@ -204,3 +204,53 @@ def test_status_codes_and_messages(dd):
         dd.Plan(8, 1500.0, -1.0, 0.0, [0.0])
     assert "tsamp" in str(e.value)
     assert dd.lib.dd_plan_maxshift(None) == -1
+
+
+def test_channeliser_host_routines_match_the_oracle(dd, oracle_lib):
+    """The library's prototype is the oracle's FP64 prototype rounded once to
+    FP32, and both count the same spectra."""
+    for M, T in [(16, 8), (32, 3), (64, 1), (128, 16), (256, 8)]:
+        got = dd.pfb_prototype(M, T)
+        want = oracle_lib.pfb_prototype(M, T).astype(np.float32)
+        assert np.array_equal(got.view(np.uint32), want.view(np.uint32)), (M, T)
+    rng = np.random.default_rng(3)
+    for _ in range(200):
+        M = int(rng.choice([16, 32, 64, 128, 256]))
+        T = int(rng.integers(1, 17))
+        nraw = int(rng.integers(0, 40 * M))
+        assert dd.channelise_nspec(nraw, M, T) == oracle_lib.pfb_nspec(nraw, M, T)
+    for bad in [(100, 8, 4), (100, 48, 4), (100, 512, 4), (100, 16, 0), (100, 16, 17),
+                (-1, 16, 4)]:
+        assert dd.lib.dd_channelise_nspec(*bad) == -1, bad
+    with pytest.raises(dd.DDError):
+        dd.pfb_prototype(1, 1)
+
+
+def test_channelise_validates_before_touching_a_gpu(dd):
+    """dd_channelise argument errors are DD_ERR_INVALID from host checks alone."""
+    P = 4096
+    good = dict(volts=P, vpitch=4096, nsub=2, nraw=1024, M=16, T=4, h=P, kind=1, scale=0.5,
+                out=P, opitch=256)
+    bad = [
+        dict(M=8), dict(M=48), dict(M=512), dict(T=0), dict(T=17),
+        dict(nsub=0), dict(nsub=65536), dict(nraw=-1),
+        dict(kind=2), dict(kind=-1),
+        dict(scale=0.0), dict(scale=-1.0), dict(scale=float("nan")), dict(scale=float("inf")),
+        dict(vpitch=4092),                    # shorter than 4*nraw
+        dict(vpitch=4098),                    # not a multiple of 4
+        dict(opitch=240),                     # shorter than 4 bytes x 61 spectra
+        dict(opitch=246),                     # not a multiple of the 4-byte element
+        dict(kind=0, opitch=512),             # FP32 elements: 16 x 61 bytes needed
+        dict(kind=0, opitch=984),             # not a multiple of 16
+        dict(volts=0), dict(h=0), dict(out=0),
+        dict(volts=P + 2), dict(h=P + 2), dict(out=P + 2),
+        dict(kind=0, opitch=1024, out=P + 4),  # FP32 output must be 16-byte aligned
+    ]
+    for b in bad:
+        a = {**good, **b}
+        st = dd.lib.dd_channelise(ctypes.c_void_p(a["volts"]), a["vpitch"], a["nsub"],
+                                  a["nraw"], a["M"], a["T"], ctypes.c_void_p(a["h"]), a["kind"],
+                                  a["scale"], ctypes.c_void_p(a["out"]), a["opitch"], None)
+        assert st == -1, b
+    # fewer than M*T raw samples: no spectra, a no-op that needs no device
+    assert dd.lib.dd_channelise(None, 252, 2, 63, 16, 4, None, 1, 0.5, None, 0, None) == 0
