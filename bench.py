@@ -337,7 +337,7 @@ def frontend_section(dd, torch, dev, w: fb.Workload, nin: int, hbm_gbs: float, n
 
 
 def channeliser_section(dd, torch, dev, hbm_gbs: float, sm_mhz: float, nsub: int = 0,
-                        reps: int = 10) -> dict:
+                        reps: int = 10, which: str = "both") -> dict:
     """dd_channelise (int8 output, the front end's element) on the two
     channeliser workloads: 64 subbands x 16 channels and 4 subbands x 256
     channels, 8 taps, the 1024 channels of the L-band front-end block.
@@ -346,10 +346,13 @@ def channeliser_section(dd, torch, dev, hbm_gbs: float, sm_mhz: float, nsub: int
     a complex sample as two fused multiply-adds) and 5*M*log2(M) for the FFT.
     The FP32 peak is 152 SMs x 128 lanes x 2 flops x the measured maximum
     SM clock.  Inputs (9.7 GB) exceed L2.  nsub > 0 keeps the first nsub
-    subbands of each workload (a smaller case for profiling)."""
+    subbands of each workload (a smaller case for profiling); which picks one
+    workload ("16ch", "256ch") or both."""
     res = {"fp32_peak_tflops": SM_COUNT * ADD_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12,
            "peak_gbs": hbm_gbs}
     for w in (fb.CHANNELISER_LBAND, fb.CHANNELISER_WIDE):
+        if which != "both" and which != f"{w.M}ch":
+            continue
         ns = w.nsub if nsub <= 0 else min(nsub, w.nsub)
         pool = fb.VoltagePool(w.seed)
         v = pool.long_rows_torch(ns, w.nraw, dev)
@@ -698,7 +701,7 @@ def run_ours(args, w):
     if not args.no_pfb and world == 1:
         line["channeliser"] = channeliser_section(dd, torch, dev, pk.get("hbm_gbs", 6800.0),
                                                   pk.get("sm_max_mhz", 2070.0),
-                                                  nsub=args.pfb_subs)
+                                                  nsub=args.pfb_subs, which=args.pfb_workload)
     if not args.no_cpu:
         line["cpu_baseline"] = cpu_oracle_sample(w)
     print(json.dumps(line), flush=True)
@@ -777,6 +780,8 @@ def main():
     ap.add_argument("--no-pfb", action="store_true", help="skip the channeliser section")
     ap.add_argument("--pfb-subs", type=int, default=0,
                     help="channeliser section on the first N subbands only (0: all)")
+    ap.add_argument("--pfb-workload", default="both", choices=["both", "16ch", "256ch"],
+                    help="channeliser workloads to run")
     ap.add_argument("--sweep", action="store_true",
                     help="run the Fig. 4 sweeps instead (one JSON line)")
     ap.add_argument("--tiles", default="", help="fixed tile shape dthr,dm_warps,time_warps,cstage")

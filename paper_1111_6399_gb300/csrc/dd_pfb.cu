@@ -28,14 +28,21 @@
 //    k1, giving y[k1 + 16*k2].  Shared memory holds the FFT index as the
 //    fastest dimension, so the 32 lanes of a warp always touch 32 different
 //    transforms: every shared-memory access is conflict-free.
-//  * Output: the two polarisations of a spectrum sit in neighbouring lanes;
-//    one shuffle pairs them into the (Xre, Xim, Yre, Yim) element -- four
-//    int8 codes, q = clamp(rint(v*scale), -127, 127) with v*scale rounded
-//    once (FMA into 1.5*2^23), or four FP32 values -- and lanes with
-//    consecutive spectra store consecutive elements of a channel row.
+//  * Packed FP32: the FIR keeps (re, im) pairs and multiplies them by (h, h)
+//    with FFMA2, and the FFT's butterflies a +- t run as FADD2 / FFMA2, so a
+//    pair of FP32 operations takes one issue slot.
+//  * Output: each transform's values go to a shared-memory staging area laid
+//    out as [channel][spectrum] -- int8 codes q = clamp(rint(v*scale), -127,
+//    127) with v*scale rounded once (FMA into 1.5*2^23), the two
+//    polarisations of a spectrum side by side, or FP32 values -- and the CTA
+//    then writes channel rows with 16-byte stores (four int8 elements, or one
+//    FP32 element, per thread).
 //  * Rounds: each round a segment emits RS spectra; the next round's raw
 //    words are loaded before the current round's DFT, so they are in flight
 //    while it runs.
+//  * Occupancy: two CTAs per SM (at most 128 registers per thread; a cap of
+//    80 for three CTAs spills and measured 24 % slower on the 16-channel
+//    workload).
 //
 // HBM traffic: each raw word is read once by the segment that uses it (plus
 // T-1 words of overlap per segment, served from L2), each output element
@@ -64,6 +71,7 @@ struct PfbArgs {
     int nr;              // rounds per CTA
     float scale;         // int8 output: codes = rint(v * scale)
     int ci8;             // 1: int8 elements (4 bytes), 0: FP32 elements (16 bytes)
+    int vec;             // int8 rows 16-byte aligned: four elements per store
     uint8_t *out;
     int64_t out_pitch;   // bytes
 };
@@ -101,7 +109,15 @@ __device__ __forceinline__ float2 cmul(float2 b, float2 w) {
     return make_float2(fmaf(b.x, w.x, -(b.y * w.y)), fmaf(b.x, w.y, b.y * w.x));
 }
 
+// Packed FP32 pairs (one FADD2 / FFMA2 / FMUL2 per pair): a + b, a - b
+// (b * -1 + a, one rounding like a subtraction), h * x + c, h * x.
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) {
+    return __ffma2_rn(b, make_float2(-1.0f, -1.0f), a);
+}
+
 // In-register forward DFT of N <= 16 points: radix-2 decimation in time.
+// Butterflies a +- t run on packed pairs; t = -i*b is a swap and a sign.
 template <int N>
 __device__ __forceinline__ void fft_reg(float2 (&v)[N]) {
 #pragma unroll
@@ -119,34 +135,43 @@ __device__ __forceinline__ void fft_reg(float2 (&v)[N]) {
         for (int i0 = 0; i0 < N; i0 += len) {
 #pragma unroll
             for (int k = 0; k < len / 2; ++k) {
+                const int tj = k * (16 / len);
                 const float2 a = v[i0 + k];
-                const float2 b = mul_w16(v[i0 + k + len / 2], k * (16 / len));
-                v[i0 + k] = make_float2(a.x + b.x, a.y + b.y);
-                v[i0 + k + len / 2] = make_float2(a.x - b.x, a.y - b.y);
+                const float2 b = v[i0 + k + len / 2];
+                if (tj == 4) {  // t = -i b = (b.y, -b.x)
+                    v[i0 + k] = make_float2(a.x + b.y, a.y - b.x);
+                    v[i0 + k + len / 2] = make_float2(a.x - b.y, a.y + b.x);
+                } else {
+                    const float2 t = mul_w16(b, tj);
+                    v[i0 + k] = add2(a, t);
+                    v[i0 + k + len / 2] = sub2(a, t);
+                }
             }
         }
     }
 }
 
-// Four signed bytes (Xre, Xim, Yre, Yim) -> FP32, exactly: byte b + 128 is
-// placed in the mantissa of 2^23 and 2^23 + 128 is subtracted.
-__device__ __forceinline__ float4 s8x4(uint32_t w) {
+// Four signed bytes (Xre, Xim, Yre, Yim) -> FP32 pairs X, Y, exactly: byte
+// b + 128 is placed in the mantissa of 2^23 and 2^23 + 128 is subtracted.
+__device__ __forceinline__ void s8x4(uint32_t w, float2 &x, float2 &y) {
     const uint32_t u = w ^ 0x80808080u;
-    const float off = 8388736.0f;  // 2^23 + 128
-    return make_float4(__uint_as_float(__byte_perm(u, 0x4b000000u, 0x7650)) - off,
-                       __uint_as_float(__byte_perm(u, 0x4b000000u, 0x7651)) - off,
-                       __uint_as_float(__byte_perm(u, 0x4b000000u, 0x7652)) - off,
-                       __uint_as_float(__byte_perm(u, 0x4b000000u, 0x7653)) - off);
+    const float2 off = make_float2(-8388736.0f, -8388736.0f);  // -(2^23 + 128)
+    x = add2(make_float2(__uint_as_float(__byte_perm(u, 0x4b000000u, 0x7650)),
+                         __uint_as_float(__byte_perm(u, 0x4b000000u, 0x7651))), off);
+    y = add2(make_float2(__uint_as_float(__byte_perm(u, 0x4b000000u, 0x7652)),
+                         __uint_as_float(__byte_perm(u, 0x4b000000u, 0x7653))), off);
 }
 
-// int8 code of v*scale: the FMA into 1.5*2^23 rounds the exact product to the
-// nearest integer (ties to even); clamped to [-127, 127]; the low byte of the
-// float's bits is the code in two's complement.
-__device__ __forceinline__ uint32_t code8(float v, float scale) {
+// int8 codes (re, im) of v*scale in the low 16 bits: the FMA into 1.5*2^23
+// rounds each exact product to the nearest integer (ties to even); clamped
+// to [-127, 127]; the low byte of each float's bits is its code in two's
+// complement.
+__device__ __forceinline__ uint32_t code16(float2 v, float2 scale2) {
     constexpr float magic = 12582912.0f;  // 1.5 * 2^23
-    float u = fmaf(v, scale, magic);
-    u = fminf(fmaxf(u, magic - 127.0f), magic + 127.0f);
-    return __float_as_uint(u) & 0xffu;
+    float2 u = __ffma2_rn(v, scale2, make_float2(magic, magic));
+    u.x = fminf(fmaxf(u.x, magic - 127.0f), magic + 127.0f);
+    u.y = fminf(fmaxf(u.y, magic - 127.0f), magic + 127.0f);
+    return __byte_perm(__float_as_uint(u.x), __float_as_uint(u.y), 0x0040);
 }
 
 template <int M, int TI>
@@ -157,15 +182,20 @@ struct Shape {
     static constexpr int NF = 2 * R;                // transforms per round
     static constexpr int ZS = NF + 2;               // float2 per branch row (conflict-free STS.128)
     static constexpr int M2 = M / kM1;
-    static constexpr int SMEM = (M * ZS + M) * 8;   // z rows + twiddle table
+    static constexpr int ZBYTES = (M * ZS + M) * 8; // z rows + twiddle table
+    // Output staging, [channel][spectrum of the round]: one 4-byte element
+    // (int8) or two float2 (FP32) per cell.
+    static constexpr int SMEM_CI8 = ZBYTES + M * R * 4;
+    static constexpr int SMEM_CF32 = ZBYTES + M * R * 16;
 };
 
-template <int M, int TI>
+template <int M, int TI, bool CI8>
 __global__ void __launch_bounds__(kThreads, TI > 8 ? 1 : 2) pfb_kernel(const PfbArgs a) {
     using S = Shape<M, TI>;
-    constexpr int NSEG = S::NSEG, RS = S::RS, NF = S::NF, ZS = S::ZS, M2 = S::M2;
+    constexpr int NSEG = S::NSEG, RS = S::RS, R = S::R, NF = S::NF, ZS = S::ZS, M2 = S::M2;
     extern __shared__ __align__(16) float2 zsm[];
     float2 *tw = zsm + M * ZS;  // W_M^r, r < M
+    uint8_t *stg = reinterpret_cast<uint8_t *>(zsm) + S::ZBYTES;
 
     const int tid = threadIdx.x;
     const int sub = blockIdx.y;
@@ -183,10 +213,12 @@ __global__ void __launch_bounds__(kThreads, TI > 8 ? 1 : 2) pfb_kernel(const Pfb
     const int g = tid / M;
     const int64_t n_first = n_cta + g * seg_len;
     const uint8_t *row = a.in + (int64_t)sub * a.in_pitch + 4 * (int64_t)p;
-    float hr[TI];
+    float2 hr[TI];  // (h, h): one packed multiplier per tap
 #pragma unroll
-    for (int t = 0; t < TI; ++t)
-        hr[t] = t < a.T ? __ldg(a.h + t * M + p) : 0.0f;
+    for (int t = 0; t < TI; ++t) {
+        const float h = t < a.T ? __ldg(a.h + t * M + p) : 0.0f;
+        hr[t] = make_float2(h, h);
+    }
     // Raw block j of this segment (blocks past the row repeat the last one:
     // they only meet zero taps or spectra that are not stored).
     auto load = [&](int64_t j) -> uint32_t {
@@ -194,19 +226,20 @@ __global__ void __launch_bounds__(kThreads, TI > 8 ? 1 : 2) pfb_kernel(const Pfb
         b = b < a.nblk ? b : a.nblk - 1;
         return __ldg(reinterpret_cast<const uint32_t *>(row + 4 * M * b));
     };
-    float4 acc[TI];
+    float2 ax[TI], ay[TI];  // per spectrum slot: X and Y partial sums
     // Raw block j (j mod TI = J at compile time) into the spectra j - t.
-    auto fir = [&](int J, float4 x) {
+    auto fir = [&](int J, uint32_t w) {
+        float2 x, y;
+        s8x4(w, x, y);
 #pragma unroll
         for (int t = 0; t < TI; ++t) {
             const int slot = ((J - t) % TI + TI) % TI;
             if (t == 0) {
-                acc[slot] = make_float4(hr[0] * x.x, hr[0] * x.y, hr[0] * x.z, hr[0] * x.w);
+                ax[slot] = __fmul2_rn(hr[0], x);
+                ay[slot] = __fmul2_rn(hr[0], y);
             } else {
-                acc[slot].x = fmaf(hr[t], x.x, acc[slot].x);
-                acc[slot].y = fmaf(hr[t], x.y, acc[slot].y);
-                acc[slot].z = fmaf(hr[t], x.z, acc[slot].z);
-                acc[slot].w = fmaf(hr[t], x.w, acc[slot].w);
+                ax[slot] = __ffma2_rn(hr[t], x, ax[slot]);
+                ay[slot] = __ffma2_rn(hr[t], y, ay[slot]);
             }
         }
     };
@@ -221,38 +254,20 @@ __global__ void __launch_bounds__(kThreads, TI > 8 ? 1 : 2) pfb_kernel(const Pfb
             xw[i] = load(TI - 1 + i);
 #pragma unroll
         for (int j = 0; j < TI - 1; ++j)
-            fir(j % TI, s8x4(wu[j]));
+            fir(j % TI, wu[j]);
     }
+    const float2 scale2 = make_float2(a.scale, a.scale);
 
-    // Output of transform f (= 2 * spectrum-in-round + polarisation) for
-    // channel bin k: the partner lane holds the other polarisation.
-    // The row pitch is re-read per transform through an opaque move, so the
-    // compiler does not keep one 64-bit row offset per channel bin live
-    // across the whole kernel.
-    auto emit_out = [&](int f, int r, int e, int k, float2 y, int64_t pitch) {
-        const int pol = f & 1;
-        const int rho = f >> 1;
-        const int64_t n = n_cta + (rho / RS) * seg_len + (int64_t)r * RS + rho % RS;
-        uint8_t *orow = a.out + ((int64_t)sub * M + ((k + M / 2) & (M - 1))) * pitch;
-        if (a.ci8) {
-            const uint32_t mine = code8(y.x, a.scale) | (code8(y.y, a.scale) << 8);
-            const uint32_t other = __shfl_xor_sync(0xffffffffu, mine, 1);
-            const uint32_t word = pol ? (other | (mine << 16)) : (mine | (other << 16));
-            if ((e & 1) == pol && n < a.nspec)
-                __stcs(reinterpret_cast<unsigned int *>(orow + 4 * n), word);
+    // Value y of transform f (= 2 * spectrum-in-round + polarisation) at bin
+    // k, into the staging cell of its channel and spectrum.
+    auto stage = [&](int f, int k, float2 y) {
+        const int c = (k + M / 2) & (M - 1);
+        if constexpr (CI8) {
+            reinterpret_cast<uint16_t *>(stg)[(c * R + (f >> 1)) * 2 + (f & 1)] =
+                (uint16_t)code16(y, scale2);
         } else {
-            const float2 other = make_float2(__shfl_xor_sync(0xffffffffu, y.x, 1),
-                                             __shfl_xor_sync(0xffffffffu, y.y, 1));
-            const float4 el = pol ? make_float4(other.x, other.y, y.x, y.y)
-                                  : make_float4(y.x, y.y, other.x, other.y);
-            if ((e & 1) == pol && n < a.nspec)
-                __stcs(reinterpret_cast<float4 *>(orow + 16 * n), el);
+            reinterpret_cast<float2 *>(stg)[(c * R + (f >> 1)) * 2 + (f & 1)] = y;
         }
-    };
-    auto opaque_pitch = [&]() {
-        int64_t v;
-        asm volatile("mov.b64 %0, %1;" : "=l"(v) : "l"(a.out_pitch));
-        return v;
     };
 
     for (int r = 0; r < a.nr; ++r) {
@@ -260,8 +275,8 @@ __global__ void __launch_bounds__(kThreads, TI > 8 ? 1 : 2) pfb_kernel(const Pfb
         // completes with block TI-1+i and leaves slot i mod TI.
 #pragma unroll
         for (int i = 0; i < RS; ++i) {
-            fir((TI - 1 + i) % TI, s8x4(xw[i]));
-            const float4 z = acc[i % TI];
+            fir((TI - 1 + i) % TI, xw[i]);
+            const float4 z = make_float4(ax[i % TI].x, ax[i % TI].y, ay[i % TI].x, ay[i % TI].y);
             *reinterpret_cast<float4 *>(&zsm[p * ZS + 2 * (g * RS + i)]) = z;
         }
         if (r + 1 < a.nr) {
@@ -281,10 +296,9 @@ __global__ void __launch_bounds__(kThreads, TI > 8 ? 1 : 2) pfb_kernel(const Pfb
                 v[p1] = zsm[(M2 * p1 + p2) * ZS + f];
             fft_reg<kM1>(v);
             if constexpr (M2 == 1) {
-                const int64_t pitch = opaque_pitch();
 #pragma unroll
                 for (int k = 0; k < kM1; ++k)
-                    emit_out(f, r, k, k, v[k], pitch);
+                    stage(f, k, v[k]);
             } else {
 #pragma unroll
                 for (int k1 = 0; k1 < kM1; ++k1) {
@@ -293,8 +307,8 @@ __global__ void __launch_bounds__(kThreads, TI > 8 ? 1 : 2) pfb_kernel(const Pfb
                 }
             }
         }
+        __syncthreads();
         if constexpr (M2 > 1) {
-            __syncthreads();
             // Pass 2: M2-point FFT over p2 for each (k1, transform f).
             for (int u = tid; u < kM1 * NF; u += kThreads) {
                 const int f = u % NF;
@@ -304,19 +318,45 @@ __global__ void __launch_bounds__(kThreads, TI > 8 ? 1 : 2) pfb_kernel(const Pfb
                 for (int p2 = 0; p2 < M2; ++p2)
                     v[p2] = zsm[(M2 * k1 + p2) * ZS + f];
                 fft_reg<M2>(v);
-                const int64_t pitch = opaque_pitch();
 #pragma unroll
                 for (int k2 = 0; k2 < M2; ++k2)
-                    emit_out(f, r, k2, k1 + kM1 * k2, v[k2], pitch);
+                    stage(f, k1 + kM1 * k2, v[k2]);
+            }
+            __syncthreads();
+        }
+
+        // Stores: channel rows of the staging area to HBM, 16 bytes per
+        // thread (four int8 elements, or one FP32 element).  The next round's
+        // FIR writes only z, so no barrier is needed after this phase.
+        constexpr int PER = CI8 ? 4 : 1;  // spectra per 16-byte store
+        for (int q = tid; q < M * (R / PER); q += kThreads) {
+            const int c = q / (R / PER);
+            const int rho = (q % (R / PER)) * PER;
+            const int64_t n = n_cta + (rho / RS) * seg_len + (int64_t)r * RS + rho % RS;
+            uint8_t *orow = a.out + ((int64_t)sub * M + c) * a.out_pitch;
+            if constexpr (CI8) {
+                const uint4 wv = *reinterpret_cast<const uint4 *>(stg + (c * R + rho) * 4);
+                if (a.vec && n + 3 < a.nspec) {
+                    __stcs(reinterpret_cast<uint4 *>(orow + 4 * n), wv);
+                } else {
+                    const uint32_t e[4] = {wv.x, wv.y, wv.z, wv.w};
+#pragma unroll
+                    for (int i = 0; i < 4; ++i)
+                        if (n + i < a.nspec)
+                            __stcs(reinterpret_cast<unsigned int *>(orow + 4 * (n + i)), e[i]);
+                }
+            } else {
+                const float4 el = *reinterpret_cast<const float4 *>(stg + (c * R + rho) * 16);
+                if (n < a.nspec)
+                    __stcs(reinterpret_cast<float4 *>(orow + 16 * n), el);
             }
         }
-        __syncthreads();
     }
 }
 
-template <int M, int TI>
+template <int M, int TI, bool CI8>
 cudaError_t launch(const PfbArgs &a, unsigned gx, unsigned gy, cudaStream_t s) {
-    constexpr int smem = Shape<M, TI>::SMEM;
+    constexpr int smem = CI8 ? Shape<M, TI>::SMEM_CI8 : Shape<M, TI>::SMEM_CF32;
     static unsigned long long attr_set = 0;  // per device
     if (smem > 48 * 1024) {
         int dev = 0;
@@ -324,7 +364,7 @@ cudaError_t launch(const PfbArgs &a, unsigned gx, unsigned gy, cudaStream_t s) {
         if (e != cudaSuccess)
             return e;
         if (dev >= 64 || !((attr_set >> dev) & 1ull)) {
-            e = cudaFuncSetAttribute(pfb_kernel<M, TI>,
+            e = cudaFuncSetAttribute(pfb_kernel<M, TI, CI8>,
                                      cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
             if (e != cudaSuccess)
                 return e;
@@ -332,19 +372,24 @@ cudaError_t launch(const PfbArgs &a, unsigned gx, unsigned gy, cudaStream_t s) {
                 attr_set |= 1ull << dev;
         }
     }
-    pfb_kernel<M, TI><<<dim3(gx, gy), kThreads, smem, s>>>(a);
+    pfb_kernel<M, TI, CI8><<<dim3(gx, gy), kThreads, smem, s>>>(a);
     return cudaGetLastError();
+}
+
+template <int M, bool CI8>
+cudaError_t launch_t(int ti, const PfbArgs &a, unsigned gx, unsigned gy, cudaStream_t s) {
+    switch (ti) {
+    case 2: return launch<M, 2, CI8>(a, gx, gy, s);
+    case 4: return launch<M, 4, CI8>(a, gx, gy, s);
+    case 8: return launch<M, 8, CI8>(a, gx, gy, s);
+    case 16: return launch<M, 16, CI8>(a, gx, gy, s);
+    }
+    return cudaErrorInvalidValue;
 }
 
 template <int M>
 cudaError_t launch_m(int ti, const PfbArgs &a, unsigned gx, unsigned gy, cudaStream_t s) {
-    switch (ti) {
-    case 2: return launch<M, 2>(a, gx, gy, s);
-    case 4: return launch<M, 4>(a, gx, gy, s);
-    case 8: return launch<M, 8>(a, gx, gy, s);
-    case 16: return launch<M, 16>(a, gx, gy, s);
-    }
-    return cudaErrorInvalidValue;
+    return a.ci8 ? launch_t<M, true>(ti, a, gx, gy, s) : launch_t<M, false>(ti, a, gx, gy, s);
 }
 
 int taps_instantiated(int T) { return T <= 2 ? 2 : T <= 4 ? 4 : T <= 8 ? 8 : 16; }
@@ -427,6 +472,7 @@ extern "C" dd_status dd_channelise(const void *volts, int64_t volts_pitch, int n
     a.nr = (int)nr;
     a.scale = scale;
     a.ci8 = out_kind == DD_PFB_CI8;
+    a.vec = ((uintptr_t)out % 16 == 0) && (out_pitch % 16 == 0);
     a.out = static_cast<uint8_t *>(out);
     a.out_pitch = out_pitch;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
