@@ -42,24 +42,28 @@ SM_COUNT = 152
 ADD_LANES_PER_SM = 128  # FP32/INT32 lanes per SM per clock
 
 
-# DRAM traffic of one de-dispersion launch from an ncu capture
-# (dram__bytes_read.sum + dram__bytes_write.sum), valid only for the kernel
-# source it was taken on (sha256 of csrc/dd_kernel.cuh) and the same workload,
-# dtype and tile shape; any other run reports traffic null.
-PROFILED_TRAFFIC = [
-    {"workload": "lband-1024ch-1024dm-131072", "dtype": "u8", "tiles": [4, 12, 1, 8, 8],
-     "kernel_sha256": "de4282c324bdf36a83c1fe1cc46f999ae07ee69b3da4a6f5babc261a6b9e5045",
-     "bytes": 151974656 + 520219904, "source": "profiles/dedisperse_lband_u8_full.md"},
-]
+# DRAM traffic of one de-dispersion step from an ncu capture
+# (dram__bytes_read.sum + dram__bytes_write.sum of its launches: the full DM
+# tiles and, where the last DM tile is at most half full, the remainder-DM
+# launch), valid only for the kernel and launch code it was taken on (sha256
+# of csrc/dd_kernel.cuh and csrc/dd_launch.cpp) and the same workload, dtype
+# and tile shape; any other run reports traffic null.
+PROFILED_TRAFFIC = []
+
+
+def _sha256(*parts) -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for rel in parts:
+        with open(os.path.join(ROOT, "paper_1111_6399_gb300", "csrc", rel), "rb") as f:
+            h.update(hashlib.sha256(f.read()).digest())
+    return h.hexdigest()
 
 
 def profiled_traffic(workload: str, dtype: str, tiles) -> dict | None:
-    import hashlib
-    path = os.path.join(ROOT, "paper_1111_6399_gb300", "csrc", "dd_kernel.cuh")
-    with open(path, "rb") as f:
-        digest = hashlib.sha256(f.read()).hexdigest()
+    digest = _sha256("dd_kernel.cuh", "dd_launch.cpp")
     for rec in PROFILED_TRAFFIC:
-        if (rec["kernel_sha256"] == digest and rec["workload"] == workload
+        if (rec["code_sha256"] == digest and rec["workload"] == workload
                 and rec["dtype"] == dtype and list(rec["tiles"]) == list(tiles)):
             return rec
     return None

@@ -91,6 +91,8 @@ struct dd_plan_s {
     std::mutex mu;
     std::map<int, dd::DevTables> dev;      // per CUDA device
     std::map<uint64_t, dd::Geometry> geo;  // per (dtype, tiles) key
+    // Remainder-DM launch per (dtype, tiles) key: (found, geometry).
+    std::map<uint64_t, std::pair<bool, dd::Geometry>> tail_geo;
 };
 
 namespace dd {
@@ -116,16 +118,30 @@ std::vector<dd_tiles> auto_tiles(dd_dtype t);
 // plan (shared-memory window bound over every DM tile and channel).
 dd_status make_geometry(dd_plan_s *p, dd_dtype t, const dd_tiles &tl, Geometry *g);
 
+// The same for the sorted DMs [d0, d0 + nd) only.
+dd_status make_geometry_range(dd_plan_s *p, dd_dtype t, const dd_tiles &tl, int d0, int nd,
+                              Geometry *g);
+
 // Geometry for the plan's current tile shape, cached.
 dd_status plan_geometry(dd_plan_s *p, dd_dtype t, Geometry *g);
+
+// Launch shape for the DMs of the last, partly filled DM tile of geometry g,
+// run as a launch of their own (see dd_plan.cpp); cached per tile shape.
+dd_status tail_geometry(dd_plan_s *p, dd_dtype t, const Geometry &g, bool *found,
+                        Geometry *tail);
 
 // Device tables for the current device, uploaded on first use.
 dd_status device_tables(dd_plan_s *p, DevTables **out);
 
 // Launch the de-dispersion kernel (dd_kernel_*.cu) for one beam on stream.
+// With split_tail, the DMs of a last DM tile that is at most half full run
+// as a second launch with their own tile shape, on a library stream forked
+// from and joined back into `stream`, so its CTAs fill the SMs the first
+// launch leaves idle in its last wave instead of padding a whole DM tile.
 dd_status launch_dedisperse(dd_plan_s *p, const Geometry &g, const DevTables &dt,
                             const void *in, dd_dtype dtype, int64_t in_pitch, int64_t nsamp_in,
-                            float *out, int64_t out_pitch, int64_t nsamp_out, void *stream);
+                            float *out, int64_t out_pitch, int64_t nsamp_out, void *stream,
+                            bool split_tail = true);
 
 void count_launch(int n = 1);
 

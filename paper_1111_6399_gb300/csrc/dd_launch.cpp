@@ -2,6 +2,7 @@
 // dispatch and the profiling-event hook.
 #include <cuda_runtime_api.h>
 
+#include <mutex>
 #include <string>
 
 #include "dd_internal.h"
@@ -13,13 +14,22 @@ namespace {
 thread_local cudaEvent_t g_prof_start = nullptr;
 thread_local cudaEvent_t g_prof_stop = nullptr;
 
-}  // namespace
+// Per-device stream for remainder-DM launches, with the fork and join events.
+// One mutex per device keeps each fork / launch / join sequence whole when
+// several host threads enqueue at once.
+struct SideStream {
+    std::mutex mu;
+    bool ready = false;
+    cudaStream_t s = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr;
+};
+SideStream g_side[64];
 
-dd_status launch_dedisperse(dd_plan_s *p, const Geometry &g, const DevTables &dt, const void *in,
-                            dd_dtype dtype, int64_t in_pitch, int64_t nsamp_in, float *out,
-                            int64_t out_pitch, int64_t nsamp_out, void *stream) {
-    if (nsamp_out == 0)
-        return DD_OK;
+// One launch over DM tiles [0, ntile_d) of geometry g, the sorted DMs from
+// d0 on.
+cudaError_t enqueue(dd_plan_s *p, const Geometry &g, const DevTables &dt, int d0, int ntile_d,
+                    const void *in, dd_dtype dtype, int64_t in_pitch, int64_t nsamp_in,
+                    float *out, int64_t out_pitch, int64_t nsamp_out, cudaStream_t s) {
     KArgs a{};
     BeamArgs &b = a.beam0;
     b.in = static_cast<const uint8_t *>(in);
@@ -29,11 +39,11 @@ dd_status launch_dedisperse(dd_plan_s *p, const Geometry &g, const DevTables &dt
     b.out_pitch = out_pitch;
     b.nsamp_out = nsamp_out;
     b.dmshift = dt.dmshift;
-    b.dm_sorted = dt.dm_sorted;
-    b.perm = dt.perm;
+    b.dm_sorted = dt.dm_sorted + d0;
+    b.perm = dt.perm + d0;
     b.tile_begin = 0;
     b.nchan = p->nchan;
-    b.ntile_d = g.ntile_d;
+    b.ntile_d = ntile_d;
     b.wp = g.wp;
     a.beams = nullptr;
     a.nbeams = 1;
@@ -48,26 +58,80 @@ dd_status launch_dedisperse(dd_plan_s *p, const Geometry &g, const DevTables &dt
     a.one = 1u;
     a.status = dt.status;
     const int64_t ntile_t = (nsamp_out + g.t_cta - 1) / g.t_cta;
-    const int64_t ntiles = ntile_t * g.ntile_d;
-    if (ntiles > 0x7fffffffLL)
-        return fail(DD_ERR_INVALID, "too many tiles for one launch");
-    a.total_tiles = ntiles;
-    cudaStream_t s = static_cast<cudaStream_t>(stream);
-    cudaError_t e = cudaSuccess;
-    if (g_prof_start)
-        cudaEventRecord(g_prof_start, s);
-    const unsigned grid = (unsigned)ntiles;
+    a.total_tiles = ntile_t * ntile_d;
+    const unsigned grid = (unsigned)a.total_tiles;
     const int dthr = g.tiles.dm_per_thread, nw = g.tiles.words_per_thread;
     switch (dtype) {
-    case DD_U8: e = launch_kernel_u8(a, grid, g.threads, g.smem, s, dthr, nw); break;
-    case DD_F16: e = launch_kernel_f16(a, grid, g.threads, g.smem, s, dthr, nw); break;
-    case DD_F32: e = launch_kernel_f32(a, grid, g.threads, g.smem, s, dthr, nw); break;
+    case DD_U8: return launch_kernel_u8(a, grid, g.threads, g.smem, s, dthr, nw);
+    case DD_F16: return launch_kernel_f16(a, grid, g.threads, g.smem, s, dthr, nw);
+    case DD_F32: return launch_kernel_f32(a, grid, g.threads, g.smem, s, dthr, nw);
     }
-    if (e != cudaSuccess)
-        return fail(DD_ERR_CUDA, std::string("kernel launch failed: ") + cudaGetErrorString(e));
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace
+
+dd_status launch_dedisperse(dd_plan_s *p, const Geometry &g, const DevTables &dt, const void *in,
+                            dd_dtype dtype, int64_t in_pitch, int64_t nsamp_in, float *out,
+                            int64_t out_pitch, int64_t nsamp_out, void *stream,
+                            bool split_tail) {
+    if (nsamp_out == 0)
+        return DD_OK;
+    const int64_t ntile_t = (nsamp_out + g.t_cta - 1) / g.t_cta;
+    if (ntile_t * g.ntile_d > 0x7fffffffLL)
+        return fail(DD_ERR_INVALID, "too many tiles for one launch");
+    bool split = false;
+    Geometry gt;
+    if (split_tail) {
+        dd_status st = tail_geometry(p, dtype, g, &split, &gt);
+        if (st != DD_OK)
+            return st;
+    }
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (g_prof_start)
+        cudaEventRecord(g_prof_start, s);
+    cudaError_t e = cudaSuccess;
+    if (!split) {
+        e = enqueue(p, g, dt, 0, g.ntile_d, in, dtype, in_pitch, nsamp_in, out, out_pitch,
+                    nsamp_out, s);
+        if (e != cudaSuccess)
+            return fail(DD_ERR_CUDA, std::string("kernel launch failed: ") + cudaGetErrorString(e));
+    } else {
+        int dev = 0;
+        if ((e = cudaGetDevice(&dev)) != cudaSuccess || dev >= 64)
+            return fail(DD_ERR_CUDA, "cudaGetDevice failed");
+        SideStream &ss = g_side[dev];
+        std::lock_guard<std::mutex> lk(ss.mu);
+        if (!ss.ready) {
+            if (cudaStreamCreateWithFlags(&ss.s, cudaStreamNonBlocking) != cudaSuccess ||
+                cudaEventCreateWithFlags(&ss.fork, cudaEventDisableTiming) != cudaSuccess ||
+                cudaEventCreateWithFlags(&ss.join, cudaEventDisableTiming) != cudaSuccess)
+                return fail(DD_ERR_CUDA, "remainder stream creation failed");
+            ss.ready = true;
+        }
+        const int d_full = (p->ndm / g.dm_cta) * g.dm_cta;
+        // Full DM tiles on the caller's stream; the remainder on the side
+        // stream, ordered after everything before it on `s`, and `s` waits
+        // for it before anything later.
+        e = cudaEventRecord(ss.fork, s);
+        if (e == cudaSuccess)
+            e = enqueue(p, g, dt, 0, d_full / g.dm_cta, in, dtype, in_pitch, nsamp_in, out,
+                        out_pitch, nsamp_out, s);
+        if (e == cudaSuccess)
+            e = cudaStreamWaitEvent(ss.s, ss.fork, 0);
+        if (e == cudaSuccess)
+            e = enqueue(p, gt, dt, d_full, gt.ntile_d, in, dtype, in_pitch, nsamp_in, out,
+                        out_pitch, nsamp_out, ss.s);
+        if (e == cudaSuccess)
+            e = cudaEventRecord(ss.join, ss.s);
+        if (e == cudaSuccess)
+            e = cudaStreamWaitEvent(s, ss.join, 0);
+        if (e != cudaSuccess)
+            return fail(DD_ERR_CUDA, std::string("kernel launch failed: ") + cudaGetErrorString(e));
+    }
     if (g_prof_stop)
         cudaEventRecord(g_prof_stop, s);
-    count_launch(1);
+    count_launch(split ? 2 : 1);
     return DD_OK;
 }
 

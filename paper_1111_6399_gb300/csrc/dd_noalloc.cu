@@ -130,6 +130,7 @@ extern "C" dd_status dd_execute_noalloc(dd_plan_t p, const void *in, dd_dtype dt
     dt.perm = reinterpret_cast<int *>(b + off_perm);
     dt.status = reinterpret_cast<int *>(b + off_status);
     dt.ndm_pad = ndm_pad;
+    // One launch: the remainder-DM split needs a library stream and events.
     return dd::launch_dedisperse(p, g, dt, in, dtype, in_pitch, nsamp_in, out, out_pitch,
-                                 nsamp_out, stream);
+                                 nsamp_out, stream, false);
 }

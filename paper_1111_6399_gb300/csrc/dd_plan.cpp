@@ -81,6 +81,13 @@ int64_t ring_smem(const Geometry &g, int64_t stage_bytes, int n) {
 }
 
 dd_status make_geometry(dd_plan_s *p, dd_dtype t, const dd_tiles &tl, Geometry *g) {
+    return make_geometry_range(p, t, tl, 0, p->ndm, g);
+}
+
+dd_status make_geometry_range(dd_plan_s *p, dd_dtype t, const dd_tiles &tl, int d0, int nd,
+                              Geometry *g) {
+    if (d0 < 0 || nd < 1 || d0 + nd > p->ndm)
+        return fail(DD_ERR_INVALID, "DM range outside the plan");
     if (!valid_dtype(t))
         return fail(DD_ERR_INVALID, "unknown dtype");
     const int dthr = tl.dm_per_thread;
@@ -113,14 +120,15 @@ dd_status make_geometry(dd_plan_s *p, dd_dtype t, const dd_tiles &tl, Geometry *
     r.dm_cta = dthr * tl.dm_warps;
     r.t_cta = r.span * tl.time_warps;
     r.threads = 32 * tl.dm_warps * tl.time_warps;
-    r.ntile_d = (p->ndm + r.dm_cta - 1) / r.dm_cta;
+    r.ntile_d = (nd + r.dm_cta - 1) / r.dm_cta;
     // Widest staged window (bytes) over every DM tile and channel: the CTA at
     // t0 reads samples [t0 + s(c,dm_min), t0 + t_cta + s(c,dm_max)) of channel
     // c, fetched from a 16-byte aligned start.
     int64_t widest = 0;
     for (int td = 0; td < r.ntile_d; ++td) {
-        float dmin = p->dm_sorted[(size_t)td * r.dm_cta];
-        float dmax = p->dm_sorted[std::min((size_t)(td + 1) * r.dm_cta, (size_t)p->ndm) - 1];
+        float dmin = p->dm_sorted[(size_t)d0 + (size_t)td * r.dm_cta];
+        float dmax = p->dm_sorted[(size_t)d0 +
+                                  std::min((size_t)(td + 1) * r.dm_cta, (size_t)nd) - 1];
         for (int c = 0; c < p->nchan; ++c) {
             int64_t smin = trunc_product(dmin, p->dmshift[c]);
             int64_t smax = trunc_product(dmax, p->dmshift[c]);
@@ -189,6 +197,54 @@ dd_status plan_geometry(dd_plan_s *p, dd_dtype t, Geometry *g) {
         return st;
     p->geo[key] = r;
     *g = r;
+    return DD_OK;
+}
+
+// The DMs of the last, partly filled DM tile as a launch of their own: a tile
+// shape with the same per-thread layout (dm_per_thread, words_per_thread) and
+// as many consumer warps, so a tile holds about the same work, but as few DM
+// columns as cover the remainder and correspondingly more time.  Used when
+// the remainder fills at most half a DM tile (padding it would waste at least
+// half of that tile's work); found[0] = false when no such shape fits.
+dd_status tail_geometry(dd_plan_s *p, dd_dtype t, const Geometry &g, bool *found,
+                        Geometry *tail) {
+    *found = false;
+    const int rem = p->ndm % g.dm_cta;
+    if (rem == 0 || 2 * rem > g.dm_cta || p->ndm < g.dm_cta)
+        return DD_OK;
+    std::lock_guard<std::mutex> lk(p->mu);
+    const uint64_t key = geo_key(t, g.tiles);
+    auto it = p->tail_geo.find(key);
+    if (it != p->tail_geo.end()) {
+        *found = it->second.first;
+        *tail = it->second.second;
+        return DD_OK;
+    }
+    const int dthr = g.tiles.dm_per_thread, nw = g.tiles.words_per_thread;
+    const int dmw = (rem + dthr - 1) / dthr;
+    const int warps = g.tiles.dm_warps * g.tiles.time_warps;
+    Geometry best;
+    bool have = false;
+    // Most time warps first; among shapes that fit, the first with three or
+    // more ring stages, else the first that fits at all.
+    for (int tw = warps / dmw; tw >= 1 && !(have && best.nstages >= 3); --tw) {
+        for (int cs = g.tiles.chan_per_stage; cs >= 4; cs = (cs / 2) & ~3) {
+            dd_tiles tl{dthr, dmw, tw, cs, nw};
+            Geometry r;
+            if (make_geometry_range(p, t, tl, p->ndm - rem, rem, &r) != DD_OK)
+                continue;
+            if (!have || (best.nstages < 3 && r.nstages >= 3)) {
+                best = r;
+                have = true;
+            }
+            if (r.nstages >= 3)
+                break;
+        }
+    }
+    p->tail_geo[key] = std::make_pair(have, best);
+    *found = have;
+    if (have)
+        *tail = best;
     return DD_OK;
 }
 

@@ -1,7 +1,6 @@
 """bench.py helpers that need no GPU: the ncu traffic record is reported only
 for the exact kernel source, workload, dtype and tile shape it was taken on,
 and the reference arm's oracle sample is bounded and well formed."""
-import hashlib
 import os
 
 import numpy as np
@@ -14,18 +13,23 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
 def test_traffic_record_matches_the_current_kernel_source():
-    src = os.path.join(ROOT, "paper_1111_6399_gb300", "csrc", "dd_kernel.cuh")
-    digest = hashlib.sha256(open(src, "rb").read()).hexdigest()
+    digest = bench._sha256("dd_kernel.cuh", "dd_launch.cpp")
     for rec in bench.PROFILED_TRAFFIC:
-        # a record whose kernel changed must not be reported
+        # a record whose kernel or launch code changed must not be reported
         got = bench.profiled_traffic(rec["workload"], rec["dtype"], rec["tiles"])
-        assert (got is rec) == (rec["kernel_sha256"] == digest)
+        assert (got is rec) == (rec["code_sha256"] == digest)
         # another tile shape or dtype never matches
         other = list(rec["tiles"])
         other[1] += 1
         assert bench.profiled_traffic(rec["workload"], rec["dtype"], other) is None
         assert bench.profiled_traffic(rec["workload"], "f32", rec["tiles"]) is None
         assert rec["bytes"] > 0 and os.path.exists(os.path.join(ROOT, rec["source"]))
+
+
+def test_traffic_digest_covers_kernel_and_launch_code():
+    one = bench._sha256("dd_kernel.cuh")
+    both = bench._sha256("dd_kernel.cuh", "dd_launch.cpp")
+    assert one != both and len(both) == 64
 
 
 def test_oracle_sample_is_bounded_and_described(oracle_lib):

@@ -106,6 +106,35 @@ def test_u8_fuzz_bit_exact(dd, oracle_lib, tiles, seed):
     assert np.array_equal(got, want)
 
 
+@pytest.mark.parametrize("ndm,launches", [(152, 2), (3 * 48 + 24, 2), (3 * 48 + 25, 1),
+                                           (144, 1), (40, 1)])
+@pytest.mark.parametrize("kind", ["u8", "f16-frac"])
+def test_remainder_dms_launch(dd, oracle_lib, ndm, launches, kind):
+    """With 48 DMs per tile, a remainder of at most 24 DMs runs as a second
+    launch of its own tile shape (two launches); a larger remainder, none, or
+    fewer DMs than one tile keep one padded launch.  Either way every cell is
+    bit-exact (uint8) or within the bound (FP16)."""
+    rng = np.random.default_rng(ndm)
+    nchan, nsamp_out = 200, 9000
+    band = (1500.0, -1.5, 64e-6)          # 300 MHz below 1.5 GHz, as the L-band beam
+    table = oracle_lib.dmshift(nchan, *band)
+    dms = rng.permutation(np.arange(ndm, dtype=np.float32) * np.float32(0.9))
+    nin = nsamp_out + oracle_lib.maxshift(table, dms) + 5
+    data = fb.random_filterbank(rng, nchan, nin, kind, pitch=(nin + 15) // 16 * 16)
+    plan = dd.Plan(nchan, *band, dms)
+    plan.set_tiles(kind[:3] if kind != "u8" else "u8", 4, 12, 1, 8)
+    n0 = dd.launch_count()
+    got = _run(dd, plan, data, nin, nsamp_out)
+    assert dd.launch_count() - n0 == launches
+    if kind == "u8":
+        want = oracle_lib.dedisperse(np.ascontiguousarray(data[:, :nin]), table, dms, nsamp_out)
+        assert np.array_equal(got, want)
+    else:
+        want, asum = oracle_lib.dedisperse(np.ascontiguousarray(data[:, :nin]), table, dms,
+                                           nsamp_out, with_abssum=True)
+        _check_float(got, want, asum)
+
+
 @pytest.mark.parametrize("kind", ["f32", "f16", "f32-frac", "f16-frac"])
 @pytest.mark.parametrize("seed", [0, 1, 2])
 def test_float_fuzz(dd, oracle_lib, kind, seed):
