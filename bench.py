@@ -48,7 +48,13 @@ ADD_LANES_PER_SM = 128  # FP32/INT32 lanes per SM per clock
 # launch), valid only for the kernel and launch code it was taken on (sha256
 # of csrc/dd_kernel.cuh and csrc/dd_launch.cpp) and the same workload, dtype
 # and tile shape; any other run reports traffic null.
-PROFILED_TRAFFIC = []
+PROFILED_TRAFFIC = [
+    {"workload": "lband-1024ch-1024dm-131072", "dtype": "u8", "tiles": [4, 12, 1, 8, 8],
+     "code_sha256": "9f85ff83641605e6e5e1f9706afb948545e8fc98285c228723dcaf4183aa76ed",
+     # main launch (1008 DMs, 2688 CTAs) + remainder launch (16 DMs, 43 CTAs)
+     "bytes": (153626368 + 511769344) + (135652352 + 3897856),
+     "source": "profiles/dedisperse_lband_u8_full.md"},
+]
 
 
 def _sha256(*parts) -> str:
@@ -669,7 +675,7 @@ def run_ours(args, w):
         "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_adds / 1e12,
                      "unit": "Tadd/s", "frac": achieved / peak_adds,
                      "traffic": prof["bytes"] if prof else None,
-                     "traffic_unit": "bytes per launch (ncu dram read + write)",
+                     "traffic_unit": "bytes per step (ncu dram read + write of its launches)",
                      "traffic_source": prof["source"] if prof else None,
                      "peak_source": f"{SM_COUNT} SMs x {ADD_LANES_PER_SM} lanes x "
                                     f"{pk.get('sm_max_mhz', 2070.0):.0f} MHz ({pk_kind} max clock)",

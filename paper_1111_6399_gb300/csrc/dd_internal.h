@@ -137,7 +137,8 @@ dd_status device_tables(dd_plan_s *p, DevTables **out);
 // With split_tail, the DMs of a last DM tile that is at most half full run
 // as a second launch with their own tile shape, on a library stream forked
 // from and joined back into `stream`, so its CTAs fill the SMs the first
-// launch leaves idle in its last wave instead of padding a whole DM tile.
+// launch leaves idle in its last wave instead of padding a whole DM tile --
+// when a count of the two launches' waves says that finishes earlier.
 dd_status launch_dedisperse(dd_plan_s *p, const Geometry &g, const DevTables &dt,
                             const void *in, dd_dtype dtype, int64_t in_pitch, int64_t nsamp_in,
                             float *out, int64_t out_pitch, int64_t nsamp_out, void *stream,
