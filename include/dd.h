@@ -149,7 +149,12 @@ dd_status dd_autotune(dd_plan_t plan, const void *in, dd_dtype dtype, int64_t in
  *   nsamp_out output samples per DM (>= 0; 0 is a no-op)
  * Validation (DD_ERR_INVALID, nothing launched): alignment rules above,
  * in_pitch >= nsamp_in, out_pitch >= nsamp_out, nsamp_in large enough.
- * The first call on a device uploads the plan's tables (synchronous copy). */
+ * The first call on a device uploads the plan's tables (synchronous copy).
+ * When the last DM tile of the plan's tile shape would be at most half full
+ * and a count of tile rounds says it finishes earlier, the DMs of that tile
+ * run as a second launch on a library-owned stream: it waits for an event
+ * recorded on `stream` before the call's work, and `stream` waits for its
+ * completion, so every later operation on `stream` sees the whole plane. */
 dd_status dd_execute(dd_plan_t plan, const void *in, dd_dtype dtype, int64_t in_pitch,
                      int64_t nsamp_in, float *out, int64_t out_pitch, int64_t nsamp_out,
                      void *stream);

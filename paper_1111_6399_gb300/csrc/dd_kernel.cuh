@@ -47,6 +47,7 @@
 // first waits, again bounded, for the copies it issued).
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -525,12 +526,18 @@ __global__ void __launch_bounds__(32 * (max_consumer_warps(DT, NW) + 1 + (ELEM <
 
     uint32_t L1[DT][NW], L2[DT][NW];                            // uint8 SWAR
     float P[DT][NW][SPW], S[DT][NW][SPW], C[DT][NW][SPW];      // floats
+    // FP16 input keeps the compensation terms of a word's two samples as one
+    // packed bf16 pair.  A compensation is a sum of FP32 rounding errors, at
+    // most about 64 * 2^-24 |S|, so its 8 significant bits move the result by
+    // less than 2^-27 |S|; the pair frees a register per output word.
+    __nv_bfloat162 C2[DT][NW];
 #pragma unroll
     for (int j = 0; j < DT; ++j)
 #pragma unroll
         for (int k = 0; k < NW; ++k) {
             L1[j][k] = 0u;
             L2[j][k] = 0u;
+            C2[j][k] = __float2bfloat162_rn(0.f);
 #pragma unroll
             for (int e = 0; e < SPW; ++e) {
                 P[j][k][e] = 0.f;
@@ -577,19 +584,34 @@ __global__ void __launch_bounds__(32 * (max_consumer_warps(DT, NW) + 1 + (ELEM <
 #pragma unroll
         for (int j = 0; j < DT; ++j)
 #pragma unroll
-            for (int k = 0; k < NW; ++k)
+            for (int k = 0; k < NW; ++k) {
+                float errs[SPW];
 #pragma unroll
                 for (int e = 0; e < SPW; ++e) {
                     // TwoSum(S, P): S + P = s + err exactly.
                     const float p = P[j][k][e];
                     const float s = __fadd_rn(S[j][k][e], p);
                     const float bp = __fsub_rn(s, S[j][k][e]);
-                    const float err = __fadd_rn(__fsub_rn(S[j][k][e], __fsub_rn(s, bp)),
-                                                __fsub_rn(p, bp));
-                    C[j][k][e] = __fadd_rn(C[j][k][e], err);
+                    errs[e] = __fadd_rn(__fsub_rn(S[j][k][e], __fsub_rn(s, bp)),
+                                        __fsub_rn(p, bp));
                     S[j][k][e] = s;
                     P[j][k][e] = 0.f;
                 }
+                if constexpr (ELEM == 2) {
+                    C2[j][k] = __hadd2(C2[j][k], __floats2bfloat162_rn(errs[0], errs[SPW - 1]));
+                } else {
+#pragma unroll
+                    for (int e = 0; e < SPW; ++e)
+                        C[j][k][e] = __fadd_rn(C[j][k][e], errs[e]);
+                }
+            }
+    };
+    // Compensation of output (j, k, e) as FP32.
+    auto comp = [&](int j, int k, int e) -> float {
+        if constexpr (ELEM == 2)
+            return e == 0 ? __low2float(C2[j][k]) : __high2float(C2[j][k]);
+        else
+            return C[j][k][e];
     };
 
     auto store_float = [&]() {
@@ -604,17 +626,18 @@ __global__ void __launch_bounds__(32 * (max_consumer_warps(DT, NW) + 1 + (ELEM <
                 if (row >= 0) {
                     if (SPW == 1) {
                         if (t < B.nsamp_out)
-                            orow[t] = __fadd_rn(S[j][k][0], C[j][k][0]);
+                            orow[t] = __fadd_rn(S[j][k][0], comp(j, k, 0));
                     } else {
                         if (t + 1 < B.nsamp_out) {
                             *reinterpret_cast<float2 *>(orow + t) =
-                                make_float2(__fadd_rn(S[j][k][0], C[j][k][0]),
-                                            __fadd_rn(S[j][k][SPW - 1], C[j][k][SPW - 1]));
+                                make_float2(__fadd_rn(S[j][k][0], comp(j, k, 0)),
+                                            __fadd_rn(S[j][k][SPW - 1], comp(j, k, SPW - 1)));
                         } else if (t < B.nsamp_out) {
-                            orow[t] = __fadd_rn(S[j][k][0], C[j][k][0]);
+                            orow[t] = __fadd_rn(S[j][k][0], comp(j, k, 0));
                         }
                     }
                 }
+                C2[j][k] = __float2bfloat162_rn(0.f);
 #pragma unroll
                 for (int e = 0; e < SPW; ++e) {
                     S[j][k][e] = 0.f;
