@@ -178,6 +178,25 @@ def test_short_rows_and_untouched_columns(dd, oracle_lib):
                 mag, M, T)
 
 
+def test_int8_rows_not_16_byte_aligned(dd, oracle_lib):
+    """A row pitch that is a multiple of 4 but not of 16 bytes takes the
+    element-by-element store path; codes equal the 16-byte path's and the
+    padding column stays untouched."""
+    M, T, nsub = 32, 4, 2
+    v = _volts(21, nsub, 32 * 1301 + 3)
+    nspec = oracle_lib.pfb_nspec(v.shape[1], M, T)
+    assert (nspec + 1) * 4 % 16 != 0
+    dev = torch.device("cuda:0")
+    vt = torch.from_numpy(v).to(dev)
+    h = torch.from_numpy(oracle_lib.pfb_prototype(M, T).astype(np.float32)).to(dev)
+    ref = dd.channelise(vt, M, T, h, kind="ci8", scale=0.05)
+    odd = torch.full((nsub * M, nspec + 1, 4), 55, dtype=torch.int8, device=dev)
+    dd.channelise(vt, M, T, h, kind="ci8", scale=0.05, out=odd)
+    torch.cuda.synchronize()
+    assert torch.equal(odd[:, :nspec], ref[:, :nspec])
+    assert bool((odd[:, nspec] == 55).all())
+
+
 def test_invalid_arguments_are_rejected(dd):
     dev = torch.device("cuda:0")
     v = torch.zeros((1, 1024, 4), dtype=torch.int8, device=dev)
