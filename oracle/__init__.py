@@ -16,7 +16,11 @@ arrays through ctypes.  Two builds are made from the same source:
 
 Definitions follow Sec. 2 of the paper (shift each channel by its dispersion
 delay, then sum over frequency, for every trial DM); the integer shift rule is
-spelled out in the C file's header.
+spelled out in the C file's header.  The same file states, beside each
+function, the stages around the search that the paper names without formulas
+(Sec. 1, Sec. 4, Sec. 5): the polyphase channeliser and its prototype filter,
+the front end (Stokes I, integration, RFI clipping, quantisation), sigproc
+unpacking and the boxcar detection search.
 """
 from __future__ import annotations
 
