@@ -153,3 +153,27 @@ def test_threaded_build_gives_the_same_bits(oracle_lib):
     v = _volts(rng, 3, 20 * M)
     h = oracle_lib.pfb_prototype(M, T)
     assert np.array_equal(oracle_lib.pfb(v, M, T, h), oracle_lib.pfb(v, M, T, h, threads=True))
+
+
+def test_long_voltage_rows_are_seeded_pool_slices():
+    """The channeliser workloads' rows (longer than the pools) are copies of
+    seeded pool slices, chunk by chunk: the same seed gives the same bytes,
+    every chunk is a contiguous slice of its row's pool, and the noise keeps
+    that pool's spread."""
+    torch = pytest.importorskip("torch")
+    import filterbank as fb
+    pool = fb.VoltagePool(5, size=1 << 16)
+    a = pool.long_rows_torch(3, 100_003, "cpu", chunk=1 << 14).numpy()
+    b = fb.VoltagePool(5, size=1 << 16).long_rows_torch(3, 100_003, "cpu", chunk=1 << 14).numpy()
+    assert a.shape == (3, 100_003, 4) and np.array_equal(a, b)
+    flat = [p.reshape(-1) for p in pool.pools]
+    for r in range(3):
+        chunk = a[r, 3 * (1 << 14):4 * (1 << 14)].reshape(-1)
+        hits = [i for i, p in enumerate(flat)
+                if any(np.array_equal(p[o:o + 64], chunk[:64])
+                       for o in range(0, len(p) - chunk.size + 1, 4))]
+        assert hits, r
+        sd = a[r].astype(np.float64).std()
+        assert min(abs(sd - s) for s in fb.VOLT_SIGMAS) < 0.05 * sd
+    w = fb.CHANNELISER_LBAND
+    assert w.nraw == (w.nspec + w.T - 1) * w.M and w.nsub * w.M == fb.LBAND.nchan
