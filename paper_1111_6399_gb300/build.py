@@ -85,8 +85,10 @@ def build(force: bool = False, verbose: bool = False) -> str:
         libdir = os.path.join(cuda, "lib64")
         if not os.path.isdir(libdir):
             libdir = os.path.join(cuda, "lib")
+        # -ldl: the header-only NVTX ranges look up a profiler's injection
+        # library with dlopen (in libc itself on glibc 2.34 and later)
         cmd = ["g++", "-shared", "-o", LIB + ".tmp", *objs, "-L", libdir, "-lcudart",
-               f"-Wl,-rpath,{libdir}", "-lpthread"]
+               f"-Wl,-rpath,{libdir}", "-lpthread", "-ldl"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             sys.stderr.write(r.stdout + r.stderr)

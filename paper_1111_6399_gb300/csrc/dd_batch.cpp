@@ -305,6 +305,7 @@ dd_status dd_batch_set_tiles(dd_batch_t b, const dd_tiles *t) {
 }
 
 dd_status dd_batch_execute(dd_batch_t b, void *stream) {
+    dd::Range nvtx_range("dd_batch_execute");
     if (!b)
         return fail(DD_ERR_INVALID, "batch is NULL");
     std::lock_guard<std::mutex> lk(b->mu);
@@ -364,6 +365,7 @@ dd_status dd_batch_sync(dd_batch_t b, void *stream) {
 
 dd_status dd_batch_autotune(dd_batch_t b, void *stream, int reps, dd_tune_result *results,
                             int max_results, int *n_results) {
+    dd::Range nvtx_range("dd_batch_autotune");
     if (!b || reps < 1)
         return fail(DD_ERR_INVALID, "bad batch or reps");
     cudaStream_t s = static_cast<cudaStream_t>(stream);

@@ -272,6 +272,7 @@ __global__ void finalize_kernel(int ndm, int64_t nsamp, int nlevels, double *mea
 extern "C" dd_status dd_detect(const float *plane, int64_t pitch, int ndm, int64_t nsamp,
                                int nlevels, int integer_valued, double *mean, double *std_out,
                                double *snr, int64_t *t_peak, void *stream) {
+    dd::Range nvtx_range("dd_detect");
     using dd::fail;
     if (ndm < 0 || nsamp < 1 || pitch < nsamp)
         return fail(DD_ERR_INVALID, "need ndm >= 0, nsamp >= 1 and pitch >= nsamp");

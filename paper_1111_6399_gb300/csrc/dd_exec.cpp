@@ -51,6 +51,7 @@ struct HostWorkspace {
 extern "C" dd_status dd_execute(dd_plan_t p, const void *in, dd_dtype dtype, int64_t in_pitch,
                                 int64_t nsamp_in, float *out, int64_t out_pitch,
                                 int64_t nsamp_out, void *stream) {
+    dd::Range nvtx_range("dd_execute");
     if (!p)
         return fail(DD_ERR_INVALID, "plan is NULL");
     dd_status st = check_layout(p, dtype, in_pitch, nsamp_in, out_pitch, nsamp_out, true);
@@ -101,6 +102,7 @@ extern "C" dd_status dd_sync(dd_plan_t p, void *stream) {
 extern "C" dd_status dd_execute_host(dd_plan_t p, const void *in_host, dd_dtype dtype,
                                      int64_t in_pitch, int64_t nsamp_in, float *out_host,
                                      int64_t out_pitch, int64_t nsamp_out) {
+    dd::Range nvtx_range("dd_execute_host");
     static std::mutex ws_mu;
     static HostWorkspace ws_by_dev[16];
     if (!p)
@@ -256,6 +258,7 @@ extern "C" dd_status dd_autotune(dd_plan_t p, const void *in, dd_dtype dtype, in
                                  int64_t nsamp_in, float *out, int64_t out_pitch,
                                  int64_t nsamp_out, void *stream, int reps,
                                  dd_tune_result *results, int max_results, int *n_results) {
+    dd::Range nvtx_range("dd_autotune");
     if (!p)
         return fail(DD_ERR_INVALID, "plan is NULL");
     dd_status st = check_layout(p, dtype, in_pitch, nsamp_in, out_pitch, nsamp_out, true);

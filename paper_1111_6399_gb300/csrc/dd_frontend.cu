@@ -461,6 +461,7 @@ extern "C" dd_status dd_frontend(const void *volts, int64_t volts_pitch, int nch
                                  int64_t nsamp_raw, int nint, double k_clip, int niter,
                                  uint8_t *out, int64_t out_pitch, void *work, int64_t work_bytes,
                                  double *mean, double *std_out, void *stream) {
+    dd::Range nvtx_range("dd_frontend");
     using dd::fail;
     if (!frontend_shape_ok(nchan, nsamp_raw, nint, niter))
         return fail(DD_ERR_INVALID, "need 1 <= nchan <= 65535, nsamp_raw >= 0, nint a power of "

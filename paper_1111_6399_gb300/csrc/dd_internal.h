@@ -8,9 +8,20 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/dd.h"
 
 namespace dd {
+
+// NVTX range over one C-ABI call, named after it, for Nsight timelines (a
+// no-op when no tool is attached).
+struct Range {
+    explicit Range(const char *name) { nvtxRangePushA(name); }
+    ~Range() { nvtxRangePop(); }
+    Range(const Range &) = delete;
+    Range &operator=(const Range &) = delete;
+};
 
 // Samples covered by one warp along time: 32 lanes x `words` 4-byte words x
 // (4 / element size) samples per word.

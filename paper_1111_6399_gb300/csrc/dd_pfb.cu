@@ -433,6 +433,7 @@ extern "C" dd_status dd_channelise(const void *volts, int64_t volts_pitch, int n
                                    int64_t nraw, int nchan_sub, int ntaps, const float *coeffs,
                                    int out_kind, float scale, void *out, int64_t out_pitch,
                                    void *stream) {
+    dd::Range nvtx_range("dd_channelise");
     using dd::fail;
     const int M = nchan_sub;
     if (!m_ok(M) || ntaps < 1 || ntaps > 16 || nsub < 1 || nsub > 65535 || nraw < 0)

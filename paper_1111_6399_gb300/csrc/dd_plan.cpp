@@ -302,6 +302,7 @@ int64_t dd_launch_count(void) { return g_launches.load(); }
 
 dd_status dd_plan(int nchan, double fch1_mhz, double foff_mhz, double tsamp_s,
                   const float *dm_list, int ndm, dd_plan_t *plan_out) {
+    dd::Range nvtx_range("dd_plan");
     using dd::fail;
     if (!plan_out)
         return fail(DD_ERR_INVALID, "plan_out is NULL");

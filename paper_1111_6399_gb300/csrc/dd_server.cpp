@@ -541,6 +541,7 @@ dd_status dd_server_add_beam(dd_server_t v, dd_plan_t plan, int64_t block_nsamp,
 
 dd_status dd_submit(dd_server_t v, int beam_id, const void *block_host, int64_t in_pitch,
                     float *out_host, int64_t out_pitch, dd_ticket *ticket) {
+    dd::Range nvtx_range("dd_submit");
     if (!v || !block_host || !out_host || !ticket)
         return fail(DD_ERR_INVALID, "NULL argument");
     std::unique_lock<std::mutex> lk(v->mu);
@@ -597,6 +598,7 @@ dd_status dd_submit(dd_server_t v, int beam_id, const void *block_host, int64_t 
 }
 
 dd_status dd_poll(dd_server_t v, dd_ticket t, int64_t *first_t, int64_t *nsamp) {
+    dd::Range nvtx_range("dd_poll");
     if (!v)
         return fail(DD_ERR_INVALID, "server is NULL");
     std::lock_guard<std::mutex> lk(v->mu);

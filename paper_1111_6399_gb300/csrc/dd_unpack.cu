@@ -157,6 +157,7 @@ cudaError_t launch_unpack(const uint8_t *in, int64_t spec_bytes, int nchan, int6
 
 extern "C" dd_status dd_unpack(const void *in, int nbits, int nchan, int64_t nsamp, uint8_t *out,
                                int64_t out_pitch, void *stream) {
+    dd::Range nvtx_range("dd_unpack");
     using dd::fail;
     if (nbits != 1 && nbits != 2 && nbits != 4 && nbits != 8)
         return fail(DD_ERR_INVALID, "nbits must be 1, 2, 4 or 8");
