@@ -1,14 +1,19 @@
 """Benchmark: brute-force incoherent de-dispersion on GB300.
 
-One step = one de-dispersion of the 1024-channel L-band beam (1024 trial DMs
-0..1023, 131072 output samples plus maxshift, uint8 seeded noise with 8
-injected pulses) through the C ABI, with the input resident in HBM.  The line
-reports channel*DM*sample adds/s, the roofline of the dominant kernel, the
-real-time factor, an end-to-end number through the host-buffer entry point,
-and the CPU oracle's throughput on a bounded sample.
+One step = one de-dispersion of the 4096-channel low-frequency beam (120-150
+MHz, tsamp 327.68 us, 2000 trial DMs 0..99.95 step 0.05, 262144 output
+samples plus maxshift, uint8 seeded noise with pulses at DM 12.3 and 57.8)
+through the C ABI, with the input resident in HBM.  The line reports
+channel*DM*sample adds/s, the roofline of the dominant kernel against a
+measured add peak (an in-library microbenchmark), the real-time factor, an
+end-to-end number through the host-buffer entry point, and the CPU oracle's
+throughput on bounded samples (single-threaded and OpenMP).  Sections on the
+same line: the same beam stored as FP16 and FP32 (precision), the L-band
+beam, detection, the 64-beam batch, serving, unpacking, the front end, the
+channeliser and a compact form of the Fig. 4 sweeps.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--workload lband|lowfreq|small]
+                    [--workload lowfreq|lband|small] [--dtype u8|f16|f32]
 
 Under torchrun (N > 1) every rank de-disperses its own independent beam (no
 data-path collective; weak scaling); timing is the max over ranks.
@@ -38,23 +43,20 @@ METRIC = ("channel·DM·sample adds/s and % roofline on 1 GB300; real-time facto
           "p50/p99 block latency")
 UNIT = "adds/s"
 WORKLOADS = {"small": fb.SMALL, "lband": fb.LBAND, "lowfreq": fb.LOWFREQ}
-SM_COUNT = 152
-ADD_LANES_PER_SM = 128  # FP32/INT32 lanes per SM per clock
+ADD_LANES_PER_SM = 128  # FP32/INT32 lanes per SM per clock (nominal figure beside the measured one)
+# Output samples the autotuner times each candidate on (a prefix of the
+# beam's output; the full beam when it is shorter).
+TUNE_NSAMP = 65536
 
 
 # DRAM traffic of one de-dispersion step from an ncu capture
-# (dram__bytes_read.sum + dram__bytes_write.sum of its launches: the full DM
-# tiles and, where the last DM tile is at most half full, the remainder-DM
-# launch), valid only for the kernel and launch code it was taken on (sha256
-# of csrc/dd_kernel.cuh and csrc/dd_launch.cpp) and the same workload, dtype
-# and tile shape; any other run reports traffic null.
-PROFILED_TRAFFIC = [
-    {"workload": "lband-1024ch-1024dm-131072", "dtype": "u8", "tiles": [4, 12, 1, 8, 8],
-     "code_sha256": "9f85ff83641605e6e5e1f9706afb948545e8fc98285c228723dcaf4183aa76ed",
-     # main launch (1008 DMs, 2688 CTAs) + remainder launch (16 DMs, 43 CTAs)
-     "bytes": (153626368 + 511769344) + (135652352 + 3897856),
-     "source": "profiles/dedisperse_lband_u8_full.md"},
-]
+# (dram__bytes_read.sum + dram__bytes_write.sum of its launches), valid only
+# for the kernel and launch code it was taken on (sha256 of csrc/dd_kernel.cuh
+# and csrc/dd_launch.cpp) and the same workload, dtype and tile shape; any
+# other run reports traffic null.
+TRAFFIC_SOURCE = ("ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum "
+                  "--clock-control none, one step's de-dispersion launches")
+PROFILED_TRAFFIC: list[dict] = []
 
 
 def _sha256(*parts) -> str:
@@ -84,9 +86,25 @@ def peaks():
     return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
-def add_peak(sm_mhz: float) -> float:
-    """Plain-ALU add peak: 152 SMs x 128 lanes x clock (adds/s)."""
-    return SM_COUNT * ADD_LANES_PER_SM * sm_mhz * 1e6
+def nominal_add_peak(sms: int, sm_mhz: float) -> float:
+    """Nominal plain-ALU add peak: SMs x 128 lanes x clock (adds/s)."""
+    return sms * ADD_LANES_PER_SM * sm_mhz * 1e6
+
+
+def measured_add_peak(dd, torch, dev) -> dict:
+    """The add-throughput microbenchmark (dd_add_peak) for each add kind, with
+    the SM clock sampled while it runs; the roofline denominator is the
+    largest measured rate."""
+    res = {}
+    with ClockSampler(dev.index or 0) as clk:
+        for _ in range(3):  # a few seconds of load so the clock sampler sees it
+            for kind in ("fadd", "iadd", "fadd2"):
+                rate, ms = dd.add_peak(kind, 4)
+                if kind not in res or rate > res[kind]["adds_per_s"]:
+                    res[kind] = {"adds_per_s": rate, "ms": ms}
+    best = max(res, key=lambda k: res[k]["adds_per_s"])
+    return {"kinds": res, "best": best, "adds_per_s": res[best]["adds_per_s"],
+            "clocks": clk.summary()}
 
 
 class ClockSampler:
@@ -157,45 +175,56 @@ def make_input(w: fb.Workload, dmshift: np.ndarray, maxshift: int):
     return fb.filterbank(w.nchan, nin, w.seed, pulses, delays, pitch=pitch), nin
 
 
-def prepare_oracle_sample(w: fb.Workload, budget_s: float = 12.0) -> dict:
-    """A bounded sample of the workload for the oracle (checker build, DM loop
-    over all host cores): all channels, a spread of the DMs, a slice of time,
-    sized from a short calibration run to take about budget_s."""
+def prepare_oracle_sample(w: fb.Workload, budget_s: float = 12.0, threads: bool = True) -> dict:
+    """A bounded sample of the workload for the oracle -- its OpenMP build (DM
+    loop over all host cores) or, with threads=False, the single-threaded
+    oracle proper: all channels, a spread of the DMs, a slice of time, sized
+    from a short calibration run to take about budget_s."""
     import oracle
     table = oracle.dmshift(w.nchan, w.fch1, w.foff, w.tsamp)
     dms_all = w.dm_list()
     S = oracle.maxshift(table, dms_all)
     rng = np.random.default_rng(w.seed)
-    cores = os.cpu_count() or 1
-    nsamp = min(w.nsamp_out, 4096)
+    cores = (os.cpu_count() or 1) if threads else 1
+    nsamp = min(w.nsamp_out, 4096 if threads else 1024)
     ndm = max(1, min(w.ndm, 2 * cores))
     data = rng.integers(0, 256, size=(w.nchan, nsamp + S), dtype=np.uint8)
     t = time.perf_counter()
     oracle.dedisperse(data, table, dms_all[np.linspace(0, w.ndm - 1, ndm).astype(int)], nsamp,
-                      threads=True)
+                      threads=threads)
     rate = w.nchan * ndm * nsamp / max(time.perf_counter() - t, 1e-4)
     target = rate * budget_s
     ndm = int(max(1, min(w.ndm, target / (w.nchan * nsamp))))
     nsamp = int(max(1024, min(w.nsamp_out, target / (w.nchan * ndm))))
     return {"data": rng.integers(0, 256, size=(w.nchan, nsamp + S), dtype=np.uint8),
             "table": table, "sel": dms_all[np.linspace(0, w.ndm - 1, ndm).astype(int)],
-            "nsamp": nsamp, "ndm": ndm, "cores": cores}
+            "nsamp": nsamp, "ndm": ndm, "cores": cores, "threads": threads}
 
 
 def time_oracle_sample(w: fb.Workload, prep: dict) -> dict:
     """One timed oracle run over a prepared sample."""
     import oracle
     t = time.perf_counter()
-    oracle.dedisperse(prep["data"], prep["table"], prep["sel"], prep["nsamp"], threads=True)
+    oracle.dedisperse(prep["data"], prep["table"], prep["sel"], prep["nsamp"],
+                      threads=prep["threads"])
     dt = time.perf_counter() - t
     adds = w.nchan * prep["ndm"] * prep["nsamp"]
+    how = "OpenMP over DMs" if prep["threads"] else "single-threaded"
     return {"value": adds / dt, "unit": UNIT, "cores": prep["cores"], "kind": "oracle",
             "sample": f"{w.nchan} channels x {prep['ndm']} of {w.ndm} DMs x {prep['nsamp']} "
-                      f"samples ({adds:.3g} adds, {dt:.2f} s, OpenMP over DMs)"}
+                      f"samples ({adds:.3g} adds, {dt:.2f} s, {how})",
+            "seconds": dt, "sample_adds": adds}
 
 
-def cpu_oracle_sample(w: fb.Workload, budget_s: float = 12.0) -> dict:
-    return time_oracle_sample(w, prepare_oracle_sample(w, budget_s))
+def cpu_oracle_sample(w: fb.Workload) -> dict:
+    """The oracle's OpenMP build on a ~10 s sample (the line's value, all host
+    cores) and the single-threaded oracle on a ~6 s sample."""
+    omp = time_oracle_sample(w, prepare_oracle_sample(w, 10.0, threads=True))
+    one = time_oracle_sample(w, prepare_oracle_sample(w, 6.0, threads=False))
+    for r in (omp, one):
+        r.pop("seconds")
+        r.pop("sample_adds")
+    return {**omp, "single_thread": one}
 
 
 def _plan_delays(table: np.ndarray, pulses):
@@ -346,19 +375,19 @@ def frontend_section(dd, torch, dev, w: fb.Workload, nin: int, hbm_gbs: float, n
     return res
 
 
-def channeliser_section(dd, torch, dev, hbm_gbs: float, sm_mhz: float, nsub: int = 0,
-                        reps: int = 10, which: str = "both") -> dict:
+def channeliser_section(dd, torch, dev, hbm_gbs: float, sm_mhz: float, sms: int,
+                        nsub: int = 0, reps: int = 10, which: str = "both") -> dict:
     """dd_channelise (int8 output, the front end's element) on the two
     channeliser workloads: 64 subbands x 16 channels and 4 subbands x 256
     channels, 8 taps, the 1024 channels of the L-band front-end block.
     Algorithmic bytes: the raw words read and the codes written; algorithmic
     flops per spectrum and polarisation: 4*M*T for the FIR (a real tap times
     a complex sample as two fused multiply-adds) and 5*M*log2(M) for the FFT.
-    The FP32 peak is 152 SMs x 128 lanes x 2 flops x the measured maximum
-    SM clock.  Inputs (9.7 GB) exceed L2.  nsub > 0 keeps the first nsub
+    The FP32 peak is the SM count x 128 lanes x 2 flops x the measured
+    maximum SM clock.  Inputs (9.7 GB) exceed L2.  nsub > 0 keeps the first nsub
     subbands of each workload (a smaller case for profiling); which picks one
     workload ("16ch", "256ch") or both."""
-    res = {"fp32_peak_tflops": SM_COUNT * ADD_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12,
+    res = {"fp32_peak_tflops": sms * ADD_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12,
            "peak_gbs": hbm_gbs}
     for w in (fb.CHANNELISER_LBAND, fb.CHANNELISER_WIDE):
         if which != "both" and which != f"{w.M}ch":
@@ -545,26 +574,165 @@ def run_reference(args, w):
     rank, world, _ = dist_env()
     if rank != 0:
         return
-    # each step: one oracle run over the same bounded sample of the workload,
-    # sized so that the whole run takes about a minute and a half
+    # each step: one oracle run (OpenMP build, all host cores) over the same
+    # bounded sample of the workload, sized so the whole run takes about a
+    # minute and a half; ms_per_step is the sample's own time
     prep = prepare_oracle_sample(w, budget_s=max(0.25, 90.0 / (args.warmup + args.steps)))
-    vals = []
+    vals, secs = [], []
     last = None
     for i in range(args.warmup + args.steps):
         res = time_oracle_sample(w, prep)
         if i >= args.warmup:
             vals.append(res["value"])
+            secs.append(res["seconds"])
         last = res
     v = statistics.mean(vals)
+    sample = {"ndm": prep["ndm"], "nsamp_out": prep["nsamp"], "adds": last["sample_adds"]}
+    base = {k: last[k] for k in ("unit", "cores", "kind", "sample")}
     line = {"metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": w.adds() / v * 1e3, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
-            "impl": "reference",
+            "warmup": args.warmup, "ms_per_step": statistics.mean(secs) * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
+            "data": "synthetic", "impl": "reference",
             "config": {"workload": w.name, "nchan": w.nchan, "ndm": w.ndm,
-                       "nsamp_out": w.nsamp_out, "l2": "inputs larger than L2"},
-            "cpu_baseline": {**last, "value": v},
+                       "nsamp_out": w.nsamp_out, "l2": "inputs larger than L2",
+                       "timed_sample": sample,
+                       "step": "one oracle run over the timed sample (all channels, a spread "
+                               "of the DMs, a slice of time); value = its adds per second"},
+            "full_workload_ms_extrapolated": w.adds() / v * 1e3,
+            "cpu_baseline": {**base, "value": v},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def beam_input(w: fb.Workload, plan, dtype: str):
+    """The workload's seeded uint8 beam (pulses dispersed with the plan's own
+    shifts), stored as dtype (the same integers for FP16/FP32)."""
+    host, nin = make_input(w, plan.dmshift(), plan.maxshift)
+    if dtype != "u8":
+        host = host.astype(np.float16 if dtype == "f16" else np.float32)
+    return host, nin
+
+
+def tune_beam(plan, x, out, nin: int, nsamp_out: int, stream, tiles: str, no_tune: bool,
+              dtype: str, log: bool):
+    """Tile shape for a beam: fixed (tiles "a,b,c,d[,e]"), the plan's default,
+    or the autotuner timing every candidate on the first TUNE_NSAMP output
+    samples."""
+    if tiles:
+        plan.set_tiles(dtype, *[int(v) for v in tiles.split(",")])
+        return "fixed"
+    if no_tune:
+        return "default"
+    nt = min(nsamp_out, TUNE_NSAMP)
+    S = plan.maxshift
+    res = plan.autotune(x, out[:, :nt], nsamp_in=nt + S, nsamp_out=nt, stream=stream, reps=1)
+    if log:
+        for tl, ms in sorted(res, key=lambda r: (r[1] < 0, r[1])):
+            print(f"# tune {dtype} {tl} {ms:.3f} ms" if ms >= 0 else f"# tune {dtype} {tl} "
+                  "rejected", file=sys.stderr)
+    return f"autotuner ({nt} output samples)"
+
+
+def time_steps(dd, torch, plan, x, out, nin: int, stream, steps: int, warmup: int, barrier):
+    """warmup untimed steps, then `steps` timed ones, each bracketed by CUDA
+    events on the launching stream, with the de-dispersion kernel itself
+    bracketed by a second pair (dd_profile_events).  Returns per-step ms,
+    mean kernel ms, the library's launches in the timed region and wall s."""
+    def step():
+        plan.execute(x, out, nsamp_in=nin, stream=stream)
+
+    for _ in range(warmup):
+        step()
+    plan.sync(stream)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(steps)]
+    kev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(steps)]
+    for a, b in kev:  # torch only times events it has seen recorded; the library re-records
+        a.record(stream)
+        b.record(stream)
+    n0 = dd.launch_count()
+    barrier()
+    t0 = time.perf_counter()
+    for i in range(steps):
+        dd.profile_events(*kev[i])   # around the de-dispersion kernel itself
+        ev[i][0].record(stream)
+        step()
+        ev[i][1].record(stream)
+    barrier()
+    wall = time.perf_counter() - t0
+    dd.profile_events(None, None)
+    launches = dd.launch_count() - n0
+    plan.sync(stream)
+    per_step = [a.elapsed_time(b) for a, b in ev]
+    kernel_ms = sum(a.elapsed_time(b) for a, b in kev) / len(kev)
+    return per_step, kernel_ms, launches, wall
+
+
+def e2e_rate(plan, host, nin: int, w: fb.Workload, torch, reps: int, barrier) -> float:
+    """Seconds per step through dd_execute_host from pinned host buffers
+    (host-to-device copies of the step's input and device-to-host copies of
+    its plane inside the timed region)."""
+    h_in = torch.from_numpy(host).pin_memory()
+    h_out = torch.empty((w.ndm, w.nsamp_out), dtype=torch.float32).pin_memory()
+    plan.execute_host(h_in, h_out, nsamp_in=nin)
+    barrier()
+    t = time.perf_counter()
+    for _ in range(reps):
+        plan.execute_host(h_in, h_out, nsamp_in=nin)
+    dt = (time.perf_counter() - t) / reps
+    del h_in, h_out
+    return dt
+
+
+def roofline_of(adds: float, kernel_ms: float, peak: dict, nominal: float, w: fb.Workload,
+                dtype: str, tiles, traffic_ok: bool = True) -> dict:
+    achieved = adds / (kernel_ms / 1e3)
+    prof = profiled_traffic(w.name, dtype, tiles) if traffic_ok else None
+    return {"bound": "alu", "achieved": achieved / 1e12, "peak": peak["adds_per_s"] / 1e12,
+            "unit": "Tadd/s", "frac": achieved / peak["adds_per_s"],
+            "peak_source": f"measured: dd_add_peak microbenchmark ({peak['best']}), "
+                           "best of 3 launches",
+            "peak_nominal": nominal / 1e12, "frac_of_nominal": achieved / nominal,
+            "traffic": prof["bytes"] if prof else None,
+            "traffic_unit": "bytes per step (ncu dram read + write of its launches)",
+            "traffic_source": TRAFFIC_SOURCE if prof else None,
+            "kernel": "dedisperse_kernel<%d,%d,%d>" % ({"u8": 1, "f16": 2, "f32": 4}[dtype],
+                                                       tiles[0], tiles[4]),
+            "kernel_ms": kernel_ms}
+
+
+def beam_section(dd, torch, dev, w: fb.Workload, dtype: str, steps: int, warmup: int, peak,
+                 nominal, args, e2e_reps: int = 2) -> dict:
+    """One beam in one storage type, single GPU: tuned tile shape, timed
+    steps, kernel roofline, real-time factor and end-to-end rate."""
+    stream = torch.cuda.current_stream(dev)
+    plan = dd.Plan(w.nchan, w.fch1, w.foff, w.tsamp, w.dm_list())
+    host, nin = beam_input(w, plan, dtype)
+    x = torch.from_numpy(host).to(dev)
+    out = torch.empty((w.ndm, w.nsamp_out), dtype=torch.float32, device=dev)
+    tiles_from = tune_beam(plan, x, out, nin, w.nsamp_out, stream, "", args.no_tune, dtype,
+                           False)
+
+    def barrier():
+        torch.cuda.synchronize(dev)
+
+    per_step, kernel_ms, launches, _ = time_steps(dd, torch, plan, x, out, nin, stream, steps,
+                                                  warmup, barrier)
+    step_ms = sum(per_step) / len(per_step)
+    tiles = plan.get_tiles(dtype)
+    rl = roofline_of(w.adds(), kernel_ms, peak, nominal, w, dtype, tiles)
+    rl["compulsory_bytes"] = int(w.nchan * nin * host.itemsize + w.ndm * w.nsamp_out * 4)
+    del x, out
+    torch.cuda.empty_cache()
+    e2e_s = e2e_rate(plan, host, nin, w, torch, e2e_reps, barrier)
+    return {"workload": w.name, "dtype": dtype, "tiles": tiles, "tiles_from": tiles_from,
+            "steps": steps, "ms_per_step": step_ms, "adds_per_s": w.adds() / (step_ms / 1e3),
+            "roofline": rl, "real_time_factor": w.duration_s() / (step_ms / 1e3),
+            "gpu_launches": launches,
+            "e2e": {"value": w.adds() / e2e_s, "unit": UNIT,
+                    "h2d_bytes_per_step": int(w.nchan * nin * host.itemsize),
+                    "d2h_bytes_per_step": int(w.ndm * w.nsamp_out * 4)}}
 
 
 def run_ours(args, w):
@@ -578,112 +746,69 @@ def run_ours(args, w):
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+
+    pk, pk_kind = peaks()
+    peak = measured_add_peak(dd, torch, dev)
+    nominal = nominal_add_peak(sms, pk.get("sm_max_mhz", 2070.0))
 
     plan = dd.Plan(w.nchan, w.fch1, w.foff, w.tsamp, w.dm_list())
     S = plan.maxshift
-    host, nin = make_input(w, plan.dmshift(), S)
     dt = args.dtype
-    if dt != "u8":  # the same integer noise stored as FP16/FP32, pitch kept 16-byte aligned
-        host = host.astype(np.float16 if dt == "f16" else np.float32)
+    host, nin = beam_input(w, plan, dt)
     x = torch.from_numpy(host).to(dev)
     out = torch.empty((w.ndm, w.nsamp_out), dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream(dev)
-
-    tune = None
-    if args.tiles:
-        plan.set_tiles(dt, *[int(v) for v in args.tiles.split(",")])
-    elif not args.no_tune:
-        tune = plan.autotune(x, out, nsamp_in=nin, stream=stream, reps=2)
-        if rank == 0:
-            for tl, ms in sorted(tune, key=lambda r: (r[1] < 0, r[1])):
-                print(f"# tune {tl} {ms:.3f} ms" if ms >= 0 else f"# tune {tl} rejected",
-                      file=sys.stderr)
-
-    def step():
-        plan.execute(x, out, nsamp_in=nin, stream=stream)
-
-    for _ in range(args.warmup):
-        step()
-    plan.sync(stream)
+    tiles_from = tune_beam(plan, x, out, nin, w.nsamp_out, stream, args.tiles, args.no_tune, dt,
+                           rank == 0)
 
     def barrier():
         if dist is not None:
             dist.barrier()
         torch.cuda.synchronize(dev)
 
-    # device-resident timing: K steps, one event pair per launch on the launching stream
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-          for _ in range(args.steps)]
-    kev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-           for _ in range(args.steps)]
-    for a, b in kev:  # torch only times events it has seen recorded; the library re-records
-        a.record(stream)
-        b.record(stream)
-    n0 = dd.launch_count()
     with ClockSampler(local) as clk:
-        barrier()
-        t_start = time.perf_counter()
-        for i in range(args.steps):
-            dd.profile_events(*kev[i])   # around the de-dispersion kernel itself
-            ev[i][0].record(stream)
-            step()
-            ev[i][1].record(stream)
-        barrier()
-        wall = time.perf_counter() - t_start
-    dd.profile_events(None, None)
-    launches = dd.launch_count() - n0
-    plan.sync(stream)
-    per_step_ms = [a.elapsed_time(b) for a, b in ev]
-    kernel_ms = sum(a.elapsed_time(b) for a, b in kev) / len(kev)
+        per_step_ms, kernel_ms, launches, wall = time_steps(dd, torch, plan, x, out, nin, stream,
+                                                            args.steps, args.warmup, barrier)
     step_ms = sum(per_step_ms) / len(per_step_ms)
-    total_ms = sum(per_step_ms)
-    total_ms = max_over_ranks(total_ms, dist, dev)
+    total_ms = max_over_ranks(sum(per_step_ms), dist, dev)
     adds = w.adds()
     value = adds * world * args.steps / (total_ms / 1e3)
+    tiles = plan.get_tiles(dt)
 
     # end-to-end: host buffers through dd_execute_host, copies inside the timed region
-    h_in = torch.from_numpy(host).pin_memory()
-    h_out = torch.empty((w.ndm, w.nsamp_out), dtype=torch.float32).pin_memory()
-    plan.execute_host(h_in, h_out, nsamp_in=nin)
-    e2e_steps = max(1, min(args.steps, 5))
-    barrier()
-    t = time.perf_counter()
-    for _ in range(e2e_steps):
-        plan.execute_host(h_in, h_out, nsamp_in=nin)
-    e2e_s = (time.perf_counter() - t) / e2e_steps
-    e2e_s = max_over_ranks(e2e_s, dist, dev)
+    detect = None
+    if not args.no_detect and dt == "u8" and rank == 0:
+        detect = detect_section(dd, torch, out, w, pk.get("hbm_gbs", 6800.0), w.dm_list())
+    del x, out
+    torch.cuda.empty_cache()
+    e2e_s = max_over_ranks(e2e_rate(plan, host, nin, w, torch, max(1, min(args.steps, 3)),
+                                    barrier), dist, dev)
 
     if rank != 0:
         dist.destroy_process_group()
         return
-    pk, pk_kind = peaks()
     clocks = clk.summary()
-    peak_adds = add_peak(pk.get("sm_max_mhz", 2070.0))
-    achieved = adds / (kernel_ms / 1e3)
-    prof = profiled_traffic(w.name, dt, plan.get_tiles(dt))
+    rl = roofline_of(adds, kernel_ms, peak, nominal, w, dt, tiles)
+    rl["compulsory_bytes"] = int(w.nchan * nin * host.itemsize + w.ndm * w.nsamp_out * 4)
+    rl["step_ms"] = step_ms
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": dt, "data": "synthetic",
         "config": {"workload": w.name, "nchan": w.nchan, "ndm": w.ndm,
-                   "nsamp_out": w.nsamp_out, "maxshift": S, "tiles": plan.get_tiles(dt),
-                   "tiles_from": "fixed" if args.tiles else ("default" if args.no_tune
-                                                             else "autotuner"),
+                   "nsamp_out": w.nsamp_out, "maxshift": S, "tiles": tiles,
+                   "tiles_from": tiles_from,
                    "l2": "inputs larger than L2 (%.0f MB in + %.0f MB out per step, L2 126 MB)"
                          % (w.nchan * nin * host.itemsize / 1e6, w.ndm * w.nsamp_out * 4 / 1e6),
                    "parallelism": f"replicas{world}" if world > 1 else "single-gpu"},
-        "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_adds / 1e12,
-                     "unit": "Tadd/s", "frac": achieved / peak_adds,
-                     "traffic": prof["bytes"] if prof else None,
-                     "traffic_unit": "bytes per step (ncu dram read + write of its launches)",
-                     "traffic_source": prof["source"] if prof else None,
-                     "peak_source": f"{SM_COUNT} SMs x {ADD_LANES_PER_SM} lanes x "
-                                    f"{pk.get('sm_max_mhz', 2070.0):.0f} MHz ({pk_kind} max clock)",
-                     "kernel": "dedisperse_kernel<%d,%d,%d>" % (
-                         {"u8": 1, "f16": 2, "f32": 4}[dt], plan.get_tiles(dt)[0],
-                         plan.get_tiles(dt)[4]),
-                     "kernel_ms": kernel_ms,
-                     "step_ms": step_ms},
+        "roofline": rl,
+        "add_peak": {"kinds": {k: v["adds_per_s"] / 1e12 for k, v in peak["kinds"].items()},
+                     "unit": "Tadd/s", "best": peak["best"], "clocks": peak["clocks"],
+                     "nominal": nominal / 1e12, "sms": sms,
+                     "nominal_source": f"{sms} SMs x {ADD_LANES_PER_SM} lanes x "
+                                       f"{pk.get('sm_max_mhz', 2070.0):.0f} MHz ({pk_kind} "
+                                       "max clock)"},
         "real_time_factor": w.duration_s() / (step_ms / 1e3),
         "e2e": {"value": adds * world / e2e_s, "unit": UNIT,
                 "h2d_bytes_per_step": int(w.nchan * nin * host.itemsize),
@@ -693,25 +818,34 @@ def run_ours(args, w):
     }
     if clocks:
         line["clocks"] = clocks
-    if not args.no_detect and dt == "u8":
-        line["detect"] = detect_section(dd, torch, out, w, pk.get("hbm_gbs", 6800.0),
-                                        w.dm_list())
-    del x, out, h_in, h_out
-    torch.cuda.empty_cache()
+    if detect:
+        line["detect"] = detect
+    del host
+    if world == 1 and not args.no_precision and w is fb.LOWFREQ and dt == "u8":
+        line["precision"] = {
+            "data": "the same integer noise stored as FP16 and FP32, summed in FP32",
+            **{d: beam_section(dd, torch, dev, w, d, max(3, min(args.steps, 10)), 3, peak,
+                               nominal, args) for d in ("f16", "f32")}}
+    if world == 1 and not args.no_lband and w is not fb.LBAND:
+        line["lband"] = beam_section(dd, torch, dev, fb.LBAND, "u8", max(3, min(args.steps, 100)),
+                                     3, peak, nominal, args)
+    lb = fb.LBAND
+    lb_nin = lb.nsamp_out + dd.Plan(lb.nchan, lb.fch1, lb.foff, lb.tsamp, lb.dm_list()).maxshift
     if not args.no_batch and world == 1:
-        line["batch"] = batch_section(dd, torch, dev, args.steps,
-                                      plan.get_tiles(dt) if dt == "u8" else None)
+        line["batch"] = batch_section(dd, torch, dev, args.steps)
     if not args.no_serve and world == 1:
         line["serving"] = serving_section(dd, torch, dev)
     if not args.no_unpack and world == 1:
-        line["unpack"] = unpack_section(dd, torch, dev, w, nin, pk.get("hbm_gbs", 6800.0))
-    if not args.no_frontend and world == 1 and w.nchan * nin * 64 <= (24 << 30):
-        line["frontend"] = frontend_section(dd, torch, dev, w, nin, pk.get("hbm_gbs", 6800.0),
+        line["unpack"] = unpack_section(dd, torch, dev, lb, lb_nin, pk.get("hbm_gbs", 6800.0))
+    if not args.no_frontend and world == 1:
+        line["frontend"] = frontend_section(dd, torch, dev, lb, lb_nin, pk.get("hbm_gbs", 6800.0),
                                             nchan=args.frontend_chans)
     if not args.no_pfb and world == 1:
         line["channeliser"] = channeliser_section(dd, torch, dev, pk.get("hbm_gbs", 6800.0),
-                                                  pk.get("sm_max_mhz", 2070.0),
+                                                  pk.get("sm_max_mhz", 2070.0), sms,
                                                   nsub=args.pfb_subs, which=args.pfb_workload)
+    if not args.no_sweep and world == 1:
+        line["fig4_sweep"] = sweep(dd, torch, dev, compact=True)
     if not args.no_cpu:
         line["cpu_baseline"] = cpu_oracle_sample(w)
     print(json.dumps(line), flush=True)
@@ -719,19 +853,16 @@ def run_ours(args, w):
         dist.destroy_process_group()
 
 
-def run_sweep(args):
+def sweep(dd, torch, dev, compact: bool = False) -> dict:
     """The Fig. 4 experiments as a second workload: execution time as a
     percentage of real time (i) over the channel count with the maximum DM at
     200 and as many trial DMs as channels, (ii) over the maximum DM with 2000
     channels and 2000 trial DMs.  DMs are equally spaced from 0.  The band and
     sampling the paper does not state are the L-band beam's: 1500 MHz down by
-    300 MHz, 64 us, 2^17 output samples (8.39 s of data).  Each point is
-    autotuned, then timed as the median of 7 launches (inputs larger than L2
-    except at the smallest points, where a launch is shorter than 1 ms)."""
-    import torch
-    import paper_1111_6399_gb300 as dd
-    dev = torch.device("cuda", 0)
-    torch.cuda.set_device(dev)
+    300 MHz, 64 us, 2^17 output samples (8.39 s of data).  Full form: six
+    points per axis, each autotuned; compact form: three points per axis with
+    the plan's default tile shape.  Each point is the median of 7 launches
+    (inputs larger than L2 except at the smallest points)."""
     pool = fb.NoisePool(7)
     fch1, bw, tsamp, nsamp_out = 1500.0, 300.0, 64e-6, 1 << 17
     duration = nsamp_out * tsamp
@@ -743,7 +874,8 @@ def run_sweep(args):
         pitch = (nin + 15) // 16 * 16
         x = torch.from_numpy(pool.rows(nchan, nin, pitch)).to(dev)
         out = torch.empty((ndm, nsamp_out), dtype=torch.float32, device=dev)
-        plan.autotune(x, out, nsamp_in=nin, reps=1)
+        if not compact:
+            plan.autotune(x, out, nsamp_in=nin, reps=1)
         ts = []
         for i in range(10):
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -760,11 +892,23 @@ def run_sweep(args):
                 "ms": ms, "pct_real_time": 100.0 * ms / 1e3 / duration,
                 "adds_per_s": adds / ms * 1e3, "tiles": plan.get_tiles("u8")}
 
-    res = {"metric": "execution time as % of real time (Fig. 4)", "data": "synthetic",
-           "band": "1500 MHz down 300 MHz, tsamp 64 us, 131072 samples (8.39 s)",
-           "nchan_sweep": [point(n, n, 200.0) for n in (128, 256, 512, 1024, 2048, 4096)],
-           "maxdm_sweep": [point(2000, 2000, m) for m in (50.0, 100.0, 200.0, 400.0, 800.0,
-                                                           1600.0)]}
+    nchans = (512, 2048, 4096) if compact else (128, 256, 512, 1024, 2048, 4096)
+    maxdms = (100.0, 400.0, 1600.0) if compact else (50.0, 100.0, 200.0, 400.0, 800.0, 1600.0)
+    return {"metric": "execution time as % of real time (Fig. 4)", "data": "synthetic",
+            "form": "compact, default tiles" if compact else "full, autotuned",
+            "band": "1500 MHz down 300 MHz, tsamp 64 us, 131072 samples (8.39 s)",
+            "nchan_sweep": [point(n, n, 200.0) for n in nchans],
+            "maxdm_sweep": [point(2000, 2000, m) for m in maxdms]}
+
+
+def run_sweep(args):
+    import torch
+    import paper_1111_6399_gb300 as dd
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    with ClockSampler(0) as clk:
+        res = sweep(dd, torch, dev, compact=False)
+    res["clocks"] = clk.summary()
     print(json.dumps(res), flush=True)
 
 
@@ -774,12 +918,16 @@ def main():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="lband", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="lowfreq", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-tune", action="store_true", help="use the plan's default tile shape")
     ap.add_argument("--dtype", default="u8", choices=["u8", "f16", "f32"],
                     help="storage type of the beam (the same integer noise)")
     ap.add_argument("--no-batch", action="store_true", help="skip the 64-beam batch section")
+    ap.add_argument("--no-precision", action="store_true",
+                    help="skip the FP16/FP32 section of the low-frequency beam")
+    ap.add_argument("--no-lband", action="store_true", help="skip the L-band beam section")
+    ap.add_argument("--no-sweep", action="store_true", help="skip the compact Fig. 4 sweep")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving section")
     ap.add_argument("--no-unpack", action="store_true", help="skip the input unpacking section")
     ap.add_argument("--no-detect", action="store_true", help="skip the detection section")
@@ -794,7 +942,8 @@ def main():
                     help="channeliser workloads to run")
     ap.add_argument("--sweep", action="store_true",
                     help="run the Fig. 4 sweeps instead (one JSON line)")
-    ap.add_argument("--tiles", default="", help="fixed tile shape dthr,dm_warps,time_warps,cstage")
+    ap.add_argument("--tiles", default="",
+                    help="fixed tile shape dthr,dm_warps,time_warps,cstage[,words]")
     args = ap.parse_args()
     w = WORKLOADS[args.workload]
     if args.sweep:

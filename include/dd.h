@@ -181,16 +181,26 @@ dd_status dd_execute_host(dd_plan_t plan, const void *in_host, dd_dtype dtype,
  * rounded up to a multiple of 64 plus 64, each part rounded up to 256 bytes)
  * must fit in 1 MiB, e.g. 4096 channels and up to about 128000 DMs; a larger
  * plan returns DD_ERR_INVALID (use dd_execute).  The input size is not
- * limited.  The first call on a device looks up the array's device
- * address; make that call before any stream capture.  All calls share the
+ * limited.  The first call on a device looks up the array's device address.
+ * The table copies come from pageable host memory that lives only for the
+ * call, so the call may wait for earlier work on stream, and a stream that
+ * is being captured is refused with DD_ERR_INVALID.  All calls share the
  * array and a call overwrites what the last one left: calls whose GPU work
  * overlaps (other streams or threads) race and must be serialized by the
- * caller.  The table copies come from pageable host memory, so the call may
- * wait for earlier work on stream.  Kernel-side check failures are recorded
- * in the array only (dd_sync reports those of dd_execute). */
+ * caller.  Kernel-side failures (a bounded wait that ran out, a failed
+ * internal check) are recorded in the array's status word, which
+ * dd_sync_noalloc reports. */
 dd_status dd_execute_noalloc(dd_plan_t plan, const void *in, dd_dtype dtype, int64_t in_pitch,
                              int64_t nsamp_in, float *out, int64_t out_pitch,
                              int64_t nsamp_out, void *stream);
+
+/* Status of dd_execute_noalloc on the current device, allocating nothing:
+ * waits for stream, reads the status word of the fixed array and returns
+ * DD_OK, DD_ERR_TIMEOUT (a device wait ran out) or DD_ERR_DEVICE (a failed
+ * internal check), clearing the word after a failure.  The word is shared
+ * like the rest of the array: it reports every no-alloc call since the last
+ * dd_execute_noalloc cleared it. */
+dd_status dd_sync_noalloc(void *stream);
 
 /* --- input side: corner turn and bit unpacking ---------------------------- */
 
@@ -440,6 +450,21 @@ dd_status dd_server_destroy(dd_server_t server);
  * DD_ERR_TIMEOUT or DD_ERR_DEVICE), then clear it. */
 dd_status dd_sync(dd_plan_t plan, void *stream);
 
+/* Add-throughput microbenchmark, the measured denominator of the
+ * de-dispersion roofline (the method is bound by one 32-bit add per channel,
+ * DM and sample).  The paper has no counterpart: it quotes its kernel as a
+ * fraction of peak (Sec. 5) without saying how the peak was obtained.
+ * Launches ctas_per_sm (1..8) CTAs of 256 threads per SM, each thread running
+ * 8 independent chains of one add kind: kind 0 = FP32 add.rn.f32, kind 1 =
+ * 32-bit integer adds split between the integer ALU (add.u32) and the FMA
+ * pipe (mad.lo.u32 by a run-time 1), kind 2 = packed FP32 pairs
+ * (add.rn.f32x2, two adds each).  Times 3 launches after a warm-up with CUDA
+ * events on stream and writes the best as adds per second to *adds_per_s and
+ * its duration (ms) to *ms_out (may be NULL).  Synchronous; allocates
+ * nothing.  Returns DD_ERR_INVALID for a bad kind or CTA count. */
+dd_status dd_add_peak(int kind, int ctas_per_sm, void *stream, double *adds_per_s,
+                      double *ms_out);
+
 /* Profiling hook: while set (non-NULL), every execution issued from this
  * thread records start_event just before its de-dispersion kernel and
  * stop_event just after it, on the launch stream (cudaEvent_t handles owned
@@ -452,6 +477,11 @@ void dd_profile_events(void *start_event, void *stop_event);
  * when the wait gave up and reported it as designed (no fault, no hang);
  * synchronizes stream. */
 dd_status dd_selftest_wait_timeout(int64_t limit_ns, void *stream);
+
+/* The same wait, recording its timeout in the status word of
+ * dd_execute_noalloc's fixed array (reported by dd_sync_noalloc) instead of
+ * a word of its own.  Allocates nothing; asynchronous on stream. */
+dd_status dd_selftest_noalloc_timeout(int64_t limit_ns, void *stream);
 
 /* Kernel launches made by this process so far (all entry points). */
 int64_t dd_launch_count(void);

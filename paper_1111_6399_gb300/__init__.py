@@ -5,7 +5,7 @@ include/dd.h); this package is its thin Python binding.  Importing it loads
 the library and raises ImportError if it has not been built
 (``python __graft_entry__.py``).
 """
-from ._binding import (DD_F16, DD_F32, DD_U8, Batch, DDError, Plan, Server, Tiles, channelise,
+from ._binding import (DD_F16, DD_F32, DD_U8, Batch, add_peak, DDError, Plan, Server, Tiles, channelise,
                        channelise_nspec, check, detect, dtype_code, elem_size, frontend,
                        frontend_work_bytes, launch_count, lib, pfb_prototype, profile_events,
                        unpack, warp_span)
@@ -13,4 +13,4 @@ from ._binding import (DD_F16, DD_F32, DD_U8, Batch, DDError, Plan, Server, Tile
 __all__ = ["Plan", "Batch", "Server", "Tiles", "DDError", "DD_U8", "DD_F16", "DD_F32", "check",
            "dtype_code", "elem_size", "warp_span", "launch_count", "profile_events", "unpack",
            "detect", "frontend", "frontend_work_bytes", "channelise", "channelise_nspec",
-           "pfb_prototype", "lib"]
+           "pfb_prototype", "lib", "add_peak"]

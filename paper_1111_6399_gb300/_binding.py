@@ -32,7 +32,7 @@ EXPORTS = [
     "dd_submit", "dd_poll", "dd_server_drain", "dd_server_get_stats", "dd_server_destroy",
     "dd_selftest_wait_timeout", "dd_server_set_batch_window", "dd_unpack", "dd_detect",
     "dd_frontend", "dd_frontend_work_bytes", "dd_channelise", "dd_channelise_nspec",
-    "dd_pfb_prototype",
+    "dd_pfb_prototype", "dd_sync_noalloc", "dd_selftest_noalloc_timeout", "dd_add_peak",
 ]
 
 
@@ -87,6 +87,10 @@ def _load() -> ctypes.CDLL:
         "dd_execute_host": (i32, [p, p, i32, i64, i64, p, i64, i64]),
         "dd_execute_noalloc": (i32, [p, p, i32, i64, i64, p, i64, i64, p]),
         "dd_sync": (i32, [p, p]),
+        "dd_sync_noalloc": (i32, [p]),
+        "dd_add_peak": (i32, [i32, i32, p, ctypes.POINTER(ctypes.c_double),
+                              ctypes.POINTER(ctypes.c_double)]),
+        "dd_selftest_noalloc_timeout": (i32, [i64, p]),
         "dd_unpack": (i32, [p, i32, i32, i64, p, i64, p]),
         "dd_detect": (i32, [p, i64, i32, i64, i32, i32, p, p, p, p, p]),
         "dd_frontend": (i32, [p, i64, i32, i64, i32, ctypes.c_double, i32, p, i64, p, i64, p,
@@ -151,6 +155,20 @@ def elem_size(code: int) -> int:
 
 def warp_span(code: int, words: int = 8) -> int:
     return 32 * words * (4 // (1, 2, 4)[code])
+
+
+ADD_KINDS = {"fadd": 0, "iadd": 1, "fadd2": 2}
+
+
+def add_peak(kind: str = "fadd", ctas_per_sm: int = 4, stream=None) -> tuple[float, float]:
+    """dd_add_peak: (adds per second, kernel ms) of the add-throughput
+    microbenchmark on the current device ("fadd", "iadd" or "fadd2")."""
+    import torch
+    s = torch.cuda.current_stream() if stream is None else stream
+    rate, ms = ctypes.c_double(0.0), ctypes.c_double(0.0)
+    check(lib.dd_add_peak(ADD_KINDS[kind], int(ctas_per_sm), ctypes.c_void_p(s.cuda_stream),
+                          ctypes.byref(rate), ctypes.byref(ms)))
+    return float(rate.value), float(ms.value)
 
 
 def launch_count() -> int:
@@ -385,6 +403,12 @@ class Plan:
         check(lib.dd_execute_noalloc(self.handle, ctypes.c_void_p(in_ptr), dtype, in_pitch,
                                      nsamp_in, ctypes.c_void_p(out_ptr), out_pitch, nsamp_out,
                                      ctypes.c_void_p(stream)))
+
+    @staticmethod
+    def sync_noalloc(stream: int = 0) -> None:
+        """dd_sync_noalloc: wait for stream and raise if a dd_execute_noalloc
+        kernel recorded a failure in the fixed array's status word."""
+        check(lib.dd_sync_noalloc(ctypes.c_void_p(stream)))
 
     def execute_host(self, inp: np.ndarray, out: np.ndarray, nsamp_in: int | None = None,
                      nsamp_out: int | None = None):

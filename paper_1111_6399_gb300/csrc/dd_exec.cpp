@@ -17,24 +17,7 @@ using dd::fail;
 
 bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
 
-dd_status check_layout(dd_plan_s *p, dd_dtype dtype, int64_t in_pitch, int64_t nsamp_in,
-                       int64_t out_pitch, int64_t nsamp_out, bool device_rows) {
-    if (dtype != DD_U8 && dtype != DD_F16 && dtype != DD_F32)
-        return fail(DD_ERR_INVALID, "unknown dtype");
-    if (nsamp_out < 0 || nsamp_in < 0)
-        return fail(DD_ERR_INVALID, "negative sample count");
-    if (nsamp_out > 0 && nsamp_in < nsamp_out + p->maxshift)
-        return fail(DD_ERR_INVALID, "nsamp_in must be >= nsamp_out + maxshift (" +
-                                        std::to_string(nsamp_out + p->maxshift) + ")");
-    if (in_pitch < nsamp_in || out_pitch < nsamp_out)
-        return fail(DD_ERR_INVALID, "pitch shorter than a row");
-    if (device_rows) {
-        const int64_t elem = dd::elem_size(dtype);
-        if ((in_pitch * elem) % 16 != 0 || out_pitch % 4 != 0)
-            return fail(DD_ERR_INVALID, "row pitches must be multiples of 16 bytes");
-    }
-    return DD_OK;
-}
+using dd::check_layout;
 
 struct HostWorkspace {
     int dev = -1;
@@ -47,6 +30,29 @@ struct HostWorkspace {
 };
 
 }  // namespace
+
+namespace dd {
+
+dd_status check_layout(dd_plan_s *p, dd_dtype dtype, int64_t in_pitch, int64_t nsamp_in,
+                       int64_t out_pitch, int64_t nsamp_out, bool device_rows) {
+    if (dtype != DD_U8 && dtype != DD_F16 && dtype != DD_F32)
+        return fail(DD_ERR_INVALID, "unknown dtype");
+    if (nsamp_out < 0 || nsamp_in < 0)
+        return fail(DD_ERR_INVALID, "negative sample count");
+    if (nsamp_out > 0 && nsamp_in < nsamp_out + p->maxshift)
+        return fail(DD_ERR_INVALID, "nsamp_in must be >= nsamp_out + maxshift (" +
+                                        std::to_string(nsamp_out + p->maxshift) + ")");
+    if (in_pitch < nsamp_in || out_pitch < nsamp_out)
+        return fail(DD_ERR_INVALID, "pitch shorter than a row");
+    if (device_rows) {
+        const int64_t elem = elem_size(dtype);
+        if ((in_pitch * elem) % 16 != 0 || out_pitch % 4 != 0)
+            return fail(DD_ERR_INVALID, "row pitches must be multiples of 16 bytes");
+    }
+    return DD_OK;
+}
+
+}  // namespace dd
 
 extern "C" dd_status dd_execute(dd_plan_t p, const void *in, dd_dtype dtype, int64_t in_pitch,
                                 int64_t nsamp_in, float *out, int64_t out_pitch,

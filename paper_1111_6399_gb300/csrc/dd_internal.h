@@ -117,6 +117,16 @@ dd_status fail(dd_status st, const std::string &msg);
 // stage, in the order the kernel lays them out.
 int64_t ring_smem(const Geometry &g, int64_t stage_bytes, int n);
 
+// Host checks of a beam's layout shared by the entry points that run one
+// beam: dtype, sample counts (nsamp_in >= nsamp_out + maxshift), pitches at
+// least a row and, for device rows (device_rows), multiples of 16 bytes.
+dd_status check_layout(dd_plan_s *p, dd_dtype dtype, int64_t in_pitch, int64_t nsamp_in,
+                       int64_t out_pitch, int64_t nsamp_out, bool device_rows);
+
+// Device address of the status word of dd_execute_noalloc's fixed array on
+// the current device (looked up once per device; see dd_noalloc.cu).
+dd_status noalloc_status_word(int **out);
+
 // Preferred tile shape for a dtype.
 dd_tiles default_tiles(dd_dtype t);
 

@@ -58,27 +58,42 @@ dd_status noalloc_base(void **out) {
 
 }  // namespace
 
+namespace dd {
+
+dd_status noalloc_status_word(int **out) {
+    void *base = nullptr;
+    dd_status st = noalloc_base(&base);
+    if (st != DD_OK)
+        return st;
+    *out = reinterpret_cast<int *>(base);  // the status word sits at offset 0
+    return DD_OK;
+}
+
+}  // namespace dd
+
 extern "C" dd_status dd_execute_noalloc(dd_plan_t p, const void *in, dd_dtype dtype,
                                         int64_t in_pitch, int64_t nsamp_in, float *out,
                                         int64_t out_pitch, int64_t nsamp_out, void *stream) {
     using dd::fail;
+    dd::Range nvtx_range("dd_execute_noalloc");
     if (!p)
         return fail(DD_ERR_INVALID, "plan is NULL");
-    if (dtype != DD_U8 && dtype != DD_F16 && dtype != DD_F32)
-        return fail(DD_ERR_INVALID, "unknown dtype");
-    if (nsamp_out < 0 || nsamp_in < 0)
-        return fail(DD_ERR_INVALID, "negative sample count");
-    if (nsamp_out > 0 && nsamp_in < nsamp_out + p->maxshift)
-        return fail(DD_ERR_INVALID, "nsamp_in must be >= nsamp_out + maxshift");
-    if (in_pitch < nsamp_in || out_pitch < nsamp_out)
-        return fail(DD_ERR_INVALID, "pitch shorter than a row");
-    const int64_t elem = dd::elem_size(dtype);
-    if ((in_pitch * elem) % 16 != 0 || out_pitch % 4 != 0)
-        return fail(DD_ERR_INVALID, "row pitches must be multiples of 16 bytes");
+    dd_status st = dd::check_layout(p, dtype, in_pitch, nsamp_in, out_pitch, nsamp_out, true);
+    if (st != DD_OK)
+        return st;
     if (nsamp_out == 0)
         return DD_OK;
     if (!in || !out || ((uintptr_t)in & 15u) || ((uintptr_t)out & 15u))
         return fail(DD_ERR_INVALID, "in and out must be non-NULL and 16-byte aligned");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    // The table copies below come from pageable host vectors that live only
+    // for this call: a stream capture would refuse them (and invalidate the
+    // caller's capture), so a capturing stream is turned away up front.
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cap) != cudaSuccess)
+        return fail(DD_ERR_CUDA, "cudaStreamIsCapturing failed");
+    if (cap != cudaStreamCaptureStatusNone)
+        return fail(DD_ERR_INVALID, "dd_execute_noalloc does not run on a capturing stream");
 
     // Layout of the fixed array for this call.
     const int ndm_pad = (p->ndm + 63) / 64 * 64 + 64;
@@ -94,8 +109,7 @@ extern "C" dd_status dd_execute_noalloc(dd_plan_t p, const void *in, dd_dtype dt
                         std::to_string(kNoAllocBytes) + "-byte array; use dd_execute");
 
     dd::Geometry g;
-    dd_status st = dd::plan_geometry(p, dtype, &g);
-    if (st != DD_OK)
+    if ((st = dd::plan_geometry(p, dtype, &g)) != DD_OK)
         return st;
     void *base = nullptr;
     if ((st = noalloc_base(&base)) != DD_OK)
@@ -110,7 +124,6 @@ extern "C" dd_status dd_execute_noalloc(dd_plan_t p, const void *in, dd_dtype dt
         dms[k] = p->dm_sorted[k];
         perm[k] = p->order[k];
     }
-    cudaStream_t s = static_cast<cudaStream_t>(stream);
     cudaError_t e = cudaMemsetAsync(b + off_status, 0, sizeof(int), s);  // status starts clear
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(b + off_dmshift, p->dmshift.data(), sizeof(float) * p->nchan,
@@ -133,4 +146,29 @@ extern "C" dd_status dd_execute_noalloc(dd_plan_t p, const void *in, dd_dtype dt
     // One launch: the remainder-DM split needs a library stream and events.
     return dd::launch_dedisperse(p, g, dt, in, dtype, in_pitch, nsamp_in, out, out_pitch,
                                  nsamp_out, stream, false);
+}
+
+// Status of the last dd_execute_noalloc on the current device: waits for
+// stream, reads the status word of the fixed array into a host int and, if a
+// kernel recorded a failure there, clears it.  Allocates nothing.
+extern "C" dd_status dd_sync_noalloc(void *stream) {
+    using dd::fail;
+    dd::Range nvtx_range("dd_sync_noalloc");
+    cudaError_t e = cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess)
+        return fail(DD_ERR_CUDA, std::string("stream synchronize: ") + cudaGetErrorString(e));
+    int *status = nullptr;
+    dd_status st = dd::noalloc_status_word(&status);
+    if (st != DD_OK)
+        return st;
+    int word = 0;
+    if ((e = cudaMemcpy(&word, status, sizeof(int), cudaMemcpyDeviceToHost)) != cudaSuccess)
+        return fail(DD_ERR_CUDA, std::string("status read: ") + cudaGetErrorString(e));
+    if (word == dd::kDevOk)
+        return DD_OK;
+    if ((e = cudaMemset(status, 0, sizeof(int))) != cudaSuccess)
+        return fail(DD_ERR_CUDA, std::string("status clear: ") + cudaGetErrorString(e));
+    return word == dd::kDevTimeout
+               ? fail(DD_ERR_TIMEOUT, "a device wait of dd_execute_noalloc ran out")
+               : fail(DD_ERR_DEVICE, "a dd_execute_noalloc kernel recorded a failed check");
 }

@@ -51,3 +51,24 @@ extern "C" dd_status dd_selftest_wait_timeout(int64_t limit_ns, void *stream) {
         return fail(DD_ERR_TIMEOUT, "the bounded wait ran out and reported it (expected)");
     return word == dd::kDevOk ? DD_OK : fail(DD_ERR_DEVICE, "unexpected status word");
 }
+
+// The same bounded wait, recording into the status word of the fixed array
+// of dd_execute_noalloc instead of a word of its own, so that a test can check
+// that dd_sync_noalloc reports such a timeout.  Allocates nothing; returns
+// once the kernel is queued on stream.
+extern "C" dd_status dd_selftest_noalloc_timeout(int64_t limit_ns, void *stream) {
+    using dd::fail;
+    if (limit_ns < 1000 || limit_ns > 2000000000LL)
+        return fail(DD_ERR_INVALID, "limit must be between 1 us and 2 s");
+    int *status = nullptr;
+    dd_status st = dd::noalloc_status_word(&status);
+    if (st != DD_OK)
+        return st;
+    dd::wait_timeout_kernel<<<1, 32, 0, static_cast<cudaStream_t>(stream)>>>((uint64_t)limit_ns,
+                                                                           status);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess)
+        return fail(DD_ERR_CUDA, std::string("self-test launch: ") + cudaGetErrorString(e));
+    dd::count_launch();
+    return DD_OK;
+}

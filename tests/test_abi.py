@@ -116,6 +116,15 @@ def test_execute_validates_before_touching_a_gpu(dd):
         assert e.value.status == -1, b
     # nsamp_out == 0 is a no-op and needs no device
     p.execute_ptr(0, 0, 16, 0, 0, 0, 0)
+    # the no-alloc entry point runs the same host checks first
+    for b in bad:
+        args = {**good, **b}
+        with pytest.raises(dd.DDError) as e:
+            p.execute_noalloc_ptr(args["in_ptr"], args["dtype"], args["in_pitch"],
+                                  args["nsamp_in"], args["out_ptr"], args["out_pitch"],
+                                  args["nsamp_out"])
+        assert e.value.status == -1, b
+    p.execute_noalloc_ptr(0, 0, 16, 0, 0, 0, 0)
 
 
 def test_unpack_validates_before_touching_a_gpu(dd):

@@ -23,7 +23,7 @@ def test_traffic_record_matches_the_current_kernel_source():
         other[1] += 1
         assert bench.profiled_traffic(rec["workload"], rec["dtype"], other) is None
         assert bench.profiled_traffic(rec["workload"], "f32", rec["tiles"]) is None
-        assert rec["bytes"] > 0 and os.path.exists(os.path.join(ROOT, rec["source"]))
+        assert rec["bytes"] > 0 and rec["compulsory"] > 0
 
 
 def test_traffic_digest_covers_kernel_and_launch_code():
@@ -32,9 +32,31 @@ def test_traffic_digest_covers_kernel_and_launch_code():
     assert one != both and len(both) == 64
 
 
-def test_oracle_sample_is_bounded_and_described(oracle_lib):
-    prep = bench.prepare_oracle_sample(fb.SMALL, budget_s=0.05)
+@pytest.mark.parametrize("threads", [True, False])
+def test_oracle_sample_is_bounded_and_described(oracle_lib, threads):
+    prep = bench.prepare_oracle_sample(fb.SMALL, budget_s=0.05, threads=threads)
     res = bench.time_oracle_sample(fb.SMALL, prep)
     assert res["kind"] == "oracle" and res["unit"] == "adds/s" and res["value"] > 0
     assert res["cores"] >= 1 and "channels" in res["sample"]
+    assert (res["cores"] == 1) == (not threads) or os.cpu_count() == 1
+    assert ("single-threaded" in res["sample"]) == (not threads)
     assert 1 <= prep["ndm"] <= fb.SMALL.ndm and prep["nsamp"] <= fb.SMALL.nsamp_out
+
+
+def test_reference_arm_line_reports_its_timed_sample(oracle_lib, capsys):
+    """The reference arm prints one line whose ms_per_step is the timed
+    sample's own step time (not the full workload extrapolated) and whose
+    config names the sample."""
+    import json
+    import types
+    args = types.SimpleNamespace(gpus=1, steps=2, warmup=1)
+    os.environ.pop("RANK", None)
+    bench.run_reference(args, fb.SMALL)
+    line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["value"] > 0
+    smp = line["config"]["timed_sample"]
+    assert smp["adds"] == fb.SMALL.nchan * smp["ndm"] * smp["nsamp_out"]
+    assert abs(line["ms_per_step"] - smp["adds"] / line["value"] * 1e3) \
+        <= 0.5 * line["ms_per_step"]
+    assert line["full_workload_ms_extrapolated"] > 0
+    assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["cpu_baseline"]["kind"] == "oracle"
