@@ -240,7 +240,7 @@ static std::vector<dd_tiles> tune_candidates(dd_dtype t) {
     std::vector<dd_tiles> out;
     if (t != DD_U8) {  // TMEM-window shapes (dd_kernel_tm.cuh)
         const int nw = t == DD_F16 ? 9 : 17;
-        for (int dw : {1, 2, 4, 8})
+        for (int dw : {1, 2, dd::kTmConsumerWarps})
             for (int cs : {4, 8, 12, 16, 24, 32})
                 out.push_back(dd_tiles{4, dw, dd::kTmConsumerWarps / dw, cs, nw});
     }

@@ -24,11 +24,14 @@
 // bf16 pair per two samples) live in TMEM next to the windows, so a thread
 // keeps only P and the loaded slices in registers.
 //
-// CTA: 8 consumer warps (two per TMEM lane quarter, 256 columns each: two
-// window buffers of 72 columns, S and C) and one producer warp, which stages
-// channel windows with TMA bulk copies (no multicast) into an mbarrier ring
-// and writes a table of shifted-window offsets, as in dd_kernel.cuh.  A tile
-// is 4*dm_warps DMs x 32*T*time_warps samples, dm_warps*time_warps = 8.  The
+// CTA: 7 consumer warps (warp w on TMEM lane quarter w % 4, columns
+// 256*(w / 4) .. +255: two window buffers of 72 columns, S and C) and one
+// producer warp, which stages channel windows with TMA bulk copies (no
+// multicast) into an mbarrier ring and writes a table of shifted-window
+// offsets, as in dd_kernel.cuh.  Eight warps leave two per SM sub-partition,
+// so a thread may hold up to 255 registers: the four slices of a row are
+// loaded before one wait.  A tile is 4*dm_warps DMs x 32*T*time_warps
+// samples, dm_warps*time_warps = 7.  The
 // host admits this shape only when every 4-DM group's shift spread D over
 // every channel is at most 72 - T columns.  TMEM (all 512 columns) is
 // allocated by consumer warp 0 at the start and freed at the end on every
@@ -41,11 +44,22 @@
 namespace dd {
 namespace {
 
-constexpr int kTmWarps = 8;        // consumer warps
-constexpr int kTmDt = 4;           // DMs per consumer thread
-constexpr int kTmWin = 72;         // TMEM columns per window buffer
-constexpr int kTmColsPerWarp = 256;
+constexpr int kTmThreadsWarps = 9;  // 4 consumers, 1 producer, 4 fillers
+constexpr int kTmProducer = 4;      // warp index of the producer
+constexpr int kTmDt = 4;            // DMs per consumer thread
+constexpr int kTmWin = 72;          // TMEM columns per window buffer
+constexpr int kTmBufs = 5;          // window buffers per lane quarter
 constexpr int kTmColsAlloc = 512;
+constexpr int kMsgLast = 1;         // the row closes its tile
+constexpr int kMsgStop = 2;         // no further rows
+
+// A filled window handed from a filler to its consumer: the shift offsets of
+// DMs 1..3 relative to DM 0 (TMEM columns), control bits and the tile.
+struct __align__(16) RowMsg {
+    int d1, d2, d3, ctl;
+    int beam, td;
+    int64_t t0;
+};
 
 __device__ __forceinline__ void tm_st8(uint32_t taddr, const uint32_t (&v)[8]) {
     asm volatile(
@@ -112,6 +126,25 @@ __device__ __forceinline__ void tm_wait_st() {
     asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
 }
 
+// Bounded wait for a fine-grained hand-off (one per row): try_wait lets the
+// hardware suspend the warp until the phase completes or a short hint
+// expires, so the loop spins without the backoff sleeps of mbar_wait (a
+// sleep of 64 ns or more per hand-off would dominate a row's work).  The
+// global timer is read every 64 tries; the limit is the kernels' 2 s.
+__device__ __noinline__ bool mbar_spin_slow(uint32_t mb, uint32_t parity) {
+    const uint64_t t0 = global_ns();
+    for (uint32_t i = 1;; ++i) {
+        if (mbar_try(mb, parity))
+            return true;
+        if ((i & 63u) == 0 && global_ns() - t0 > kWaitLimitNs)
+            return false;
+    }
+}
+
+__device__ __forceinline__ bool mbar_spin(uint32_t mb, uint32_t parity) {
+    return mbar_try(mb, parity) || mbar_spin_slow(mb, parity);
+}
+
 // (a0, a1) += (b0, b1) as one packed FP32 pair add (two IEEE adds, each
 // rounded to nearest even).
 __device__ __forceinline__ void fadd2(float &a0, float &a1, float b0, float b1) {
@@ -119,6 +152,34 @@ __device__ __forceinline__ void fadd2(float &a0, float &a1, float b0, float b1) 
         "add.rn.f32x2 x, x, y; mov.b64 {%0, %1}, x; }"
         : "+f"(a0), "+f"(a1)
         : "f"(b0), "f"(b1));
+}
+
+// Columns c .. c+17 of a TMEM lane as 9 packed FP32 pairs (64-bit values).
+__device__ __forceinline__ void tm_ld18p(uint32_t taddr, uint64_t (&v)[9]) {
+    asm volatile(
+        "{ .reg .b32 r<18>;\n\t"
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {r0, r1, r2, r3, r4, r5, r6, r7, r8, r9, r10, "
+        "r11, r12, r13, r14, r15}, [%9];\n\t"
+        "tcgen05.ld.sync.aligned.32x32b.x2.b32 {r16, r17}, [%10];\n\t"
+        "mov.b64 %0, {r0, r1}; mov.b64 %1, {r2, r3}; mov.b64 %2, {r4, r5}; "
+        "mov.b64 %3, {r6, r7}; mov.b64 %4, {r8, r9}; mov.b64 %5, {r10, r11}; "
+        "mov.b64 %6, {r12, r13}; mov.b64 %7, {r14, r15}; mov.b64 %8, {r16, r17}; }"
+        : "=l"(v[0]), "=l"(v[1]), "=l"(v[2]), "=l"(v[3]), "=l"(v[4]), "=l"(v[5]), "=l"(v[6]),
+          "=l"(v[7]), "=l"(v[8])
+        : "r"(taddr), "r"(taddr + 16u)
+        : "memory");
+}
+
+__device__ __forceinline__ void reg_fence(uint64_t &v) { asm volatile("" : "+l"(v)); }
+
+// a += b for packed FP32 pairs (two IEEE adds, each rounded to nearest even).
+__device__ __forceinline__ void fadd2p(uint64_t &a, uint64_t b) {
+    asm("add.rn.f32x2 %0, %0, %1;" : "+l"(a) : "l"(b));
+}
+
+__device__ __forceinline__ float pair_lo(uint64_t v) { return __uint_as_float((uint32_t)v); }
+__device__ __forceinline__ float pair_hi(uint64_t v) {
+    return __uint_as_float((uint32_t)(v >> 32));
 }
 
 __device__ __forceinline__ float half_lo(uint32_t w) {
@@ -134,16 +195,19 @@ __device__ __forceinline__ float half_hi(uint32_t w) {
 }
 
 // ---------------------------------------------------------------------------
-// ELEM = 2 (FP16) or 4 (FP32).  Warps 0..7 consume, warp 8 produces.
+// ELEM = 2 (FP16) or 4 (FP32).  Warps 0-3 consume (warp q on TMEM lane
+// quarter q), warp 4 produces, warps 5-8 fill (the filler of quarter q is
+// warp 8 for q = 0, else warp 4 + q).
 // ---------------------------------------------------------------------------
 template <int ELEM>
-__global__ void __launch_bounds__(32 * (kTmWarps + 1), 1)
+__global__ void __launch_bounds__(32 * kTmThreadsWarps, 1)
     dedisperse_tm_kernel(const __grid_constant__ KArgs a) {
     constexpr int T = ELEM == 4 ? 17 : 18;  // output samples per thread and DM
     constexpr int SPAN = 32 * T;            // samples per warp
     constexpr int NP = (T + 1) / 2;         // FP32 pairs per DM (last one half used for T odd)
-    constexpr int SCOL = 2 * kTmWin;        // TMEM column of S within a warp's 256
+    constexpr int SCOL = kTmBufs * kTmWin;  // TMEM column of S
     constexpr int CCOL = SCOL + kTmDt * T;  // TMEM column of C (bf16 pairs)
+    static_assert(CCOL + kTmDt * NP <= kTmColsAlloc, "TMEM columns");
 
     extern __shared__ __align__(128) uint8_t smem[];
     const int tid = threadIdx.x;
@@ -160,14 +224,24 @@ __global__ void __launch_bounds__(32 * (kTmWarps + 1), 1)
         smem + nst * stage_bytes + ((nst * tab_stride * 4 + 15) & ~15));
     uint64_t *mbar = reinterpret_cast<uint64_t *>(reinterpret_cast<uint8_t *>(meta) +
                                                   nst * kStageMetaBytes);
-    uint32_t *tm_slot = reinterpret_cast<uint32_t *>(mbar + 2 * nst);
+    // Window hand-off, per lane quarter and TMEM buffer: wfull (filler ->
+    // consumer) and wempty (consumer -> filler), then the row messages.
+    uint64_t *wbar = mbar + 2 * nst;
+    RowMsg *msgs = reinterpret_cast<RowMsg *>(wbar + 2 * 4 * kTmBufs);
+    uint32_t *tm_slot = reinterpret_cast<uint32_t *>(msgs + 4 * kTmBufs);
     const uint32_t full0 = smem_addr(&mbar[0]);
     const uint32_t empty0 = smem_addr(&mbar[nst]);
+    const uint32_t wfull0 = smem_addr(&wbar[0]);
+    const uint32_t wempty0 = smem_addr(&wbar[4 * kTmBufs]);
 
     if (tid == 0) {
         for (int b = 0; b < nst; ++b) {
             mbar_init(full0 + 8 * b, 1);
-            mbar_init(empty0 + 8 * b, kTmWarps);
+            mbar_init(empty0 + 8 * b, 4);  // the four fillers
+        }
+        for (int i = 0; i < 4 * kTmBufs; ++i) {
+            mbar_init(wfull0 + 8 * i, 1);
+            mbar_init(wempty0 + 8 * i, 1);
         }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -182,7 +256,7 @@ __global__ void __launch_bounds__(32 * (kTmWarps + 1), 1)
     }
     __syncthreads();
 
-    if (warp == kTmWarps) {
+    if (warp == kTmProducer) {
         // ------------------------------ producer ------------------------------
         // As in dd_kernel.cuh, with one copy per row (no byte phases) and the
         // offset table laid out [row][DM] so a consumer fetches its 4 DMs with
@@ -343,102 +417,225 @@ __global__ void __launch_bounds__(32 * (kTmWarps + 1), 1)
         return;
     }
 
-    // ------------------------------- consumers --------------------------------
+
+    // ---------------------- consumers and fillers (TMEM) ----------------------
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tm_base = *tm_slot;
-    // This warp's TMEM lanes (its quarter) and columns.
-    const uint32_t tm = tm_base + ((uint32_t)(32 * (warp & 3)) << 16) +
-                        (uint32_t)(kTmColsPerWarp * (warp >> 2));
-    const int wdi = warp % a.dm_warps;
-    const int wti = warp / a.dm_warps;
-    const int kw = wdi * kTmDt;                  // first DM column of this thread
+    const int q = warp & 3;  // TMEM lane quarter
+    const uint32_t tm = tm_base + ((uint32_t)(32 * q) << 16);
+    const int wdi = q % a.dm_warps;
+    const int wti = q / a.dm_warps;
+    const int kw = wdi * kTmDt;                  // first DM column of quarter q's threads
     const int lane_t = wti * SPAN + T * lane;    // first sample of this thread in the tile
+    const uint32_t my_wfull = wfull0 + 8 * kTmBufs * q;
+    const uint32_t my_wempty = wempty0 + 8 * kTmBufs * q;
+    RowMsg *my_msgs = msgs + kTmBufs * q;
 
-    float P[kTmDt][2 * NP];
-#pragma unroll
-    for (int j = 0; j < kTmDt; ++j)
-#pragma unroll
-        for (int i = 0; i < 2 * NP; ++i)
-            P[j][i] = 0.f;
-
-    // Window fill: the union of the 4 DMs' windows of one row, from shared
-    // memory into window buffer `wb` of this thread's TMEM lane, as FP32.
-    // Returns nothing; the caller waits for the stores before reading.
-    auto fill = [&](int4 o, int wb) {
-        const int d = (o.w - o.x) / ELEM;  // shift spread of the 4 DMs (host-bounded)
-        const int n = T + d;               // samples to stage
-        const uint32_t tw = tm + (uint32_t)(kTmWin * wb);
-        if constexpr (ELEM == 4) {
-            const uint32_t *p = reinterpret_cast<const uint32_t *>(smem + o.x) + lane_t;
-            for (int m = 0; m < n; m += 8) {
-                uint32_t v[8];
-#pragma unroll
-                for (int i = 0; i < 8; ++i)
-                    v[i] = p[m + i];
-                tm_st8(tw + (uint32_t)m, v);
+    if (warp > kTmProducer) {
+        // ------------------------------- filler -------------------------------
+        // Walks the stages like the consumers of dd_kernel.cuh, and for each row
+        // copies the union window of quarter q's 4 DMs from shared memory into
+        // the next free TMEM buffer (as FP32), then hands it over with the
+        // row's shift offsets.
+        int64_t g = 0;
+        int bq = 0;          // ring buffer
+        uint32_t ph = 0u;    // ring phase
+        for (;;) {
+            const int slot = (int)(g % nst);
+            if (!mbar_wait(full0 + 8 * slot, (uint32_t)((g / nst) & 1))) {
+                record(a.status, kDevTimeout);
+                break;
             }
-        } else {
-            const int byte0 = o.x + 2 * lane_t;  // lane_t even: the phase is warp-uniform
-            const uint32_t *p = reinterpret_cast<const uint32_t *>(smem + (byte0 & ~3));
-            const bool odd = (byte0 & 2) != 0;
-            for (int m = 0; m < n; m += 8) {
-                uint32_t w[5];
-#pragma unroll
-                for (int i = 0; i < 5; ++i)
-                    w[i] = p[m / 2 + i];
-                uint32_t v[8];
-#pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    const uint32_t h2 = odd ? prmt(w[i], w[i + 1], 0x5432u) : w[i];
-                    v[2 * i] = __float_as_uint(half_lo(h2));
-                    v[2 * i + 1] = __float_as_uint(half_hi(h2));
+            const StageMeta m = meta[slot];
+            const int nrows = m.beam < 0 ? 0 : min(cstage, beam_at(a, m.beam).nchan - m.st * cstage);
+            for (int r = 0; r <= nrows; ++r) {
+                // r == nrows: nothing more in this stage (a terminating stage
+                // sends its message here)
+                if (r == nrows && m.beam >= 0)
+                    break;
+                if (!mbar_spin(my_wempty + 8 * bq, ph ^ 1u)) {
+                    record(a.status, kDevTimeout);
+                    g = -1;
+                    break;
                 }
-                tm_st8(tw + (uint32_t)m, v);
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                RowMsg msg;
+                if (m.beam < 0) {
+                    msg.d1 = msg.d2 = msg.d3 = 0;
+                    msg.ctl = kMsgStop;
+                    msg.beam = msg.td = 0;
+                    msg.t0 = 0;
+                } else {
+                    const int4 o = *reinterpret_cast<const int4 *>(atab + slot * tab_stride +
+                                                                   r * dm_cta + kw);
+                    const int n = T + (o.w - o.x) / ELEM;
+                    const uint32_t tw = tm + (uint32_t)(kTmWin * bq);
+                    if constexpr (ELEM == 4) {
+                        const uint32_t *p = reinterpret_cast<const uint32_t *>(smem + o.x) + lane_t;
+#pragma unroll 1
+                        for (int mm = 0; mm < n; mm += 8) {
+                            uint32_t v[8];
+#pragma unroll
+                            for (int i = 0; i < 8; ++i)
+                                v[i] = p[mm + i];
+                            tm_st8(tw + (uint32_t)mm, v);
+                        }
+                    } else {
+                        const int byte0 = o.x + 2 * lane_t;  // lane_t even: uniform phase
+                        const uint32_t *p = reinterpret_cast<const uint32_t *>(smem + (byte0 & ~3));
+                        const uint32_t sel = (byte0 & 2) ? 0x5432u : 0x3210u;
+#pragma unroll 1
+                        for (int mm = 0; mm < n; mm += 8) {
+                            uint32_t w[5];
+#pragma unroll
+                            for (int i = 0; i < 5; ++i)
+                                w[i] = p[mm / 2 + i];
+                            uint32_t v[8];
+#pragma unroll
+                            for (int i = 0; i < 4; ++i) {
+                                const uint32_t h2 = prmt(w[i], w[i + 1], sel);
+                                v[2 * i] = __float_as_uint(half_lo(h2));
+                                v[2 * i + 1] = __float_as_uint(half_hi(h2));
+                            }
+                            tm_st8(tw + (uint32_t)mm, v);
+                        }
+                    }
+                    msg.d1 = (o.y - o.x) / ELEM;
+                    msg.d2 = (o.z - o.x) / ELEM;
+                    msg.d3 = (o.w - o.x) / ELEM;
+                    msg.ctl = (m.st + 1 == m.nstage && r + 1 == nrows) ? kMsgLast : 0;
+                    msg.beam = m.beam;
+                    msg.td = m.td;
+                    msg.t0 = m.t0;
+                }
+                tm_wait_st();
+                asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+                if (lane == 0)
+                    my_msgs[bq] = msg;
+                __syncwarp();
+                if (lane == 0)
+                    mbar_arrive(my_wfull + 8 * bq);
+                if (++bq == kTmBufs) {
+                    bq = 0;
+                    ph ^= 1u;
+                }
+                if (m.beam < 0)
+                    break;
             }
+            if (g < 0 || m.beam < 0)
+                break;
+            // every shared-memory read of this stage is done: release it
+            __syncwarp();
+            if (lane == 0)
+                mbar_arrive(empty0 + 8 * slot);
+            ++g;
         }
-    };
-
-    // Add row slices of DM j (columns off .. off+T-1 of window wb) into P[j].
-    auto add_dm = [&](int j, int wb, int off) {
-        const uint32_t tw = tm + (uint32_t)(kTmWin * wb + off);
-        uint32_t v[16];
-        uint32_t e0 = 0u, e1 = 0u;
-        tm_ld16(tw, v, 0);
-        if constexpr (T == 17)
-            e0 = tm_ld1(tw + 16u);
-        else
-            tm_ld2(tw + 16u, e0, e1);
-        tm_wait_ld();
-        reg_fence(v);
-        reg_fence(e0);
-        reg_fence(e1);
+    } else {
+        // ------------------------------ consumer ------------------------------
+        uint64_t P[kTmDt][NP];
 #pragma unroll
-        for (int i = 0; i < 8; ++i)
-            fadd2(P[j][2 * i], P[j][2 * i + 1], __uint_as_float(v[2 * i]),
-                  __uint_as_float(v[2 * i + 1]));
-        if constexpr (T == 17)
-            P[j][16] = __fadd_rn(P[j][16], __uint_as_float(e0));
-        else
-            fadd2(P[j][16], P[j][17], __uint_as_float(e0), __uint_as_float(e1));
-    };
-
-    // Close a block of channels: S + P by TwoSum into (S, C); on the first
-    // block of a tile S = P and C = 0.  P is cleared.
-    auto close_block = [&](bool first_block) {
+        for (int j = 0; j < kTmDt; ++j)
 #pragma unroll
-        for (int j = 0; j < kTmDt; ++j) {
-            const uint32_t ts = tm + (uint32_t)(SCOL + j * T);
-            const uint32_t tc = tm + (uint32_t)(CCOL + j * NP);
-            uint32_t s[2 * NP];
-            uint32_t c[NP];
-            if (first_block) {
+            for (int i = 0; i < NP; ++i)
+                P[j][i] = 0ull;
+        // Close a block of channels: S + P by TwoSum into (S, C); on the first
+        // block of a tile S = P and C = 0.  P is cleared.
+        auto close_block = [&](bool first_block) {
 #pragma unroll
-                for (int i = 0; i < T; ++i)
-                    s[i] = __float_as_uint(P[j][i]);
+            for (int j = 0; j < kTmDt; ++j) {
+                const uint32_t ts = tm + (uint32_t)(SCOL + j * T);
+                const uint32_t tc = tm + (uint32_t)(CCOL + j * NP);
+                uint32_t s[2 * NP];
+                uint32_t c[NP];
+                if (first_block) {
+#pragma unroll
+                    for (int i = 0; i < T; ++i)
+                        s[i] = __float_as_uint((i & 1) ? pair_hi(P[j][i / 2]) : pair_lo(P[j][i / 2]));
+#pragma unroll
+                    for (int i = 0; i < NP; ++i)
+                        c[i] = 0u;
+                } else {
+                    uint32_t v[16], w[8];
+                    uint32_t s16 = 0u, s17 = 0u, c8x = 0u;
+                    tm_ld16(ts, v, 0);
+                    if constexpr (T == 17)
+                        s16 = tm_ld1(ts + 16u);
+                    else
+                        tm_ld2(ts + 16u, s16, s17);
+                    // C: NP = 9 columns (x8 + x1)
+                    asm volatile(
+                        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, "
+                        "[%8];"
+                        : "=r"(w[0]), "=r"(w[1]), "=r"(w[2]), "=r"(w[3]), "=r"(w[4]), "=r"(w[5]),
+                          "=r"(w[6]), "=r"(w[7])
+                        : "r"(tc)
+                        : "memory");
+                    c8x = tm_ld1(tc + 8u);
+                    tm_wait_ld();
+                    reg_fence(v);
+                    reg_fence(w);
+                    reg_fence(s16);
+                    reg_fence(s17);
+                    reg_fence(c8x);
+#pragma unroll
+                    for (int i = 0; i < 16; ++i)
+                        s[i] = v[i];
+                    s[16] = s16;
+                    if constexpr (T == 18)
+                        s[17] = s17;
+#pragma unroll
+                    for (int i = 0; i < 8; ++i)
+                        c[i] = w[i];
+                    c[8] = c8x;
+#pragma unroll
+                    for (int i = 0; i < T; ++i) {
+                        const float S0 = __uint_as_float(s[i]);
+                        const float p = (i & 1) ? pair_hi(P[j][i / 2]) : pair_lo(P[j][i / 2]);
+                        const float sum = __fadd_rn(S0, p);
+                        const float bp = __fsub_rn(sum, S0);
+                        const float err = __fadd_rn(__fsub_rn(S0, __fsub_rn(sum, bp)),
+                                                    __fsub_rn(p, bp));
+                        s[i] = __float_as_uint(sum);
+                        // C of samples 2q, 2q+1 as a packed bf16 pair
+                        __nv_bfloat162 cc = *reinterpret_cast<__nv_bfloat162 *>(&c[i / 2]);
+                        const __nv_bfloat162 e = (i & 1) ? __floats2bfloat162_rn(0.f, err)
+                                                         : __floats2bfloat162_rn(err, 0.f);
+                        cc = __hadd2(cc, e);
+                        c[i / 2] = *reinterpret_cast<uint32_t *>(&cc);
+                    }
+                }
 #pragma unroll
                 for (int i = 0; i < NP; ++i)
-                    c[i] = 0u;
-            } else {
+                    P[j][i] = 0ull;
+                uint32_t s8[8], c8[8];
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    s8[i] = s[i];
+                    c8[i] = c[i];
+                }
+                tm_st8(ts, s8);
+#pragma unroll
+                for (int i = 0; i < 8; ++i)
+                    s8[i] = s[8 + i];
+                tm_st8(ts + 8u, s8);
+                if constexpr (T == 17)
+                    tm_st1(ts + 16u, s[16]);
+                else
+                    tm_st2(ts + 16u, s[16], s[17]);
+                tm_st8(tc, c8);
+                tm_st1(tc + 8u, c[8]);
+            }
+            tm_wait_st();
+        };
+
+        // Store S + C of the tile (after its last block) to the output rows.
+        auto store_tile = [&](const BeamArgs &B, int kthr, int64_t t_first) {
+#pragma unroll
+            for (int j = 0; j < kTmDt; ++j) {
+                const int row = B.perm[kthr + j];
+                const uint32_t ts = tm + (uint32_t)(SCOL + j * T);
+                const uint32_t tc = tm + (uint32_t)(CCOL + j * NP);
+                uint32_t s[2 * NP], c[NP];
                 uint32_t v[16], w[8];
                 uint32_t s16 = 0u, s17 = 0u, c8x = 0u;
                 tm_ld16(ts, v, 0);
@@ -446,10 +643,8 @@ __global__ void __launch_bounds__(32 * (kTmWarps + 1), 1)
                     s16 = tm_ld1(ts + 16u);
                 else
                     tm_ld2(ts + 16u, s16, s17);
-                // C: NP = 9 columns (x8 + x1)
                 asm volatile(
-                    "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, "
-                    "[%8];"
+                    "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
                     : "=r"(w[0]), "=r"(w[1]), "=r"(w[2]), "=r"(w[3]), "=r"(w[4]), "=r"(w[5]),
                       "=r"(w[6]), "=r"(w[7])
                     : "r"(tc)
@@ -465,190 +660,97 @@ __global__ void __launch_bounds__(32 * (kTmWarps + 1), 1)
                 for (int i = 0; i < 16; ++i)
                     s[i] = v[i];
                 s[16] = s16;
-                if constexpr (T == 18)
-                    s[17] = s17;
+                s[17] = s17;
 #pragma unroll
                 for (int i = 0; i < 8; ++i)
                     c[i] = w[i];
                 c[8] = c8x;
+                if (row < 0)
+                    continue;
+                float *orow = B.out + (int64_t)row * B.out_pitch;
 #pragma unroll
                 for (int i = 0; i < T; ++i) {
-                    const float S0 = __uint_as_float(s[i]);
-                    const float p = P[j][i];
-                    const float sum = __fadd_rn(S0, p);
-                    const float bp = __fsub_rn(sum, S0);
-                    const float err = __fadd_rn(__fsub_rn(S0, __fsub_rn(sum, bp)),
-                                                __fsub_rn(p, bp));
-                    s[i] = __float_as_uint(sum);
-                    // C of samples 2q, 2q+1 as a packed bf16 pair
-                    __nv_bfloat162 cc = *reinterpret_cast<__nv_bfloat162 *>(&c[i / 2]);
-                    const __nv_bfloat162 e = (i & 1) ? __floats2bfloat162_rn(0.f, err)
-                                                     : __floats2bfloat162_rn(err, 0.f);
-                    cc = __hadd2(cc, e);
-                    c[i / 2] = *reinterpret_cast<uint32_t *>(&cc);
+                    const __nv_bfloat162 cc = *reinterpret_cast<const __nv_bfloat162 *>(&c[i / 2]);
+                    const float comp = (i & 1) ? __high2float(cc) : __low2float(cc);
+                    const int64_t t = t_first + i;
+                    if (t < B.nsamp_out)
+                        orow[t] = __fadd_rn(__uint_as_float(s[i]), comp);
                 }
             }
-#pragma unroll
-            for (int i = 0; i < 2 * NP; ++i)
-                P[j][i] = 0.f;
-            uint32_t s8[8], c8[8];
-#pragma unroll
-            for (int i = 0; i < 8; ++i) {
-                s8[i] = s[i];
-                c8[i] = c[i];
-            }
-            tm_st8(ts, s8);
-#pragma unroll
-            for (int i = 0; i < 8; ++i)
-                s8[i] = s[8 + i];
-            tm_st8(ts + 8u, s8);
-            if constexpr (T == 17)
-                tm_st1(ts + 16u, s[16]);
-            else
-                tm_st2(ts + 16u, s[16], s[17]);
-            tm_st8(tc, c8);
-            tm_st1(tc + 8u, c[8]);
-        }
-        tm_wait_st();
-    };
+        };
 
-    // Store S + C of the tile (after its last block) to the output rows.
-    auto store_tile = [&](const BeamArgs &B, int kthr, int64_t t_first) {
-#pragma unroll
-        for (int j = 0; j < kTmDt; ++j) {
-            const int row = B.perm[kthr + j];
-            const uint32_t ts = tm + (uint32_t)(SCOL + j * T);
-            const uint32_t tc = tm + (uint32_t)(CCOL + j * NP);
-            uint32_t s[2 * NP], c[NP];
-            uint32_t v[16], w[8];
-            uint32_t s16 = 0u, s17 = 0u, c8x = 0u;
-            tm_ld16(ts, v, 0);
-            if constexpr (T == 17)
-                s16 = tm_ld1(ts + 16u);
-            else
-                tm_ld2(ts + 16u, s16, s17);
-            asm volatile(
-                "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
-                : "=r"(w[0]), "=r"(w[1]), "=r"(w[2]), "=r"(w[3]), "=r"(w[4]), "=r"(w[5]),
-                  "=r"(w[6]), "=r"(w[7])
-                : "r"(tc)
-                : "memory");
-            c8x = tm_ld1(tc + 8u);
-            tm_wait_ld();
-            reg_fence(v);
-            reg_fence(w);
-            reg_fence(s16);
-            reg_fence(s17);
-            reg_fence(c8x);
-#pragma unroll
-            for (int i = 0; i < 16; ++i)
-                s[i] = v[i];
-            s[16] = s16;
-            s[17] = s17;
-#pragma unroll
-            for (int i = 0; i < 8; ++i)
-                c[i] = w[i];
-            c[8] = c8x;
-            if (row < 0)
-                continue;
-            float *orow = B.out + (int64_t)row * B.out_pitch;
-#pragma unroll
-            for (int i = 0; i < T; ++i) {
-                const __nv_bfloat162 cc = *reinterpret_cast<const __nv_bfloat162 *>(&c[i / 2]);
-                const float comp = (i & 1) ? __high2float(cc) : __low2float(cc);
-                const int64_t t = t_first + i;
-                if (t < B.nsamp_out)
-                    orow[t] = __fadd_rn(__uint_as_float(s[i]), comp);
-            }
-        }
-    };
 
-    int64_t g = 0;  // stages consumed
-    bool failed = false;
-    for (;;) {
-        // First stage of the next tile.
-        int b = (int)(g % nst);
-        if (!mbar_wait(full0 + 8 * b, (uint32_t)((g / nst) & 1))) {
-            record(a.status, kDevTimeout);
-            failed = true;
-            break;
-        }
-        const StageMeta m0 = meta[b];
-        if (m0.beam < 0)
-            break;  // no further tile
-        const BeamArgs &B = beam_at(a, m0.beam);
-        const int kthr = m0.td * dm_cta + kw;
-        const int nrows = B.nchan;
-        const int nstage = m0.nstage;
-        // rows of stage st: min(cstage, nchan - st*cstage)
-        auto rows_in = [&](int st) { return min(cstage, nrows - st * cstage); };
-        const int *tb = atab + b * tab_stride;
-        int st = 0, r = 0;
-        int4 o = *reinterpret_cast<const int4 *>(tb + r * dm_cta + kw);
-        fill(o, 0);
-        if (rows_in(0) == 1) {
-            __syncwarp();
-            if (lane == 0)
-                mbar_arrive(empty0 + 8 * b);
-        }
+        int bq = 0;
+        uint32_t ph = 0u;
         int since = 0;
         bool first_block = true;
-        for (int q = 0; q < nrows; ++q) {
-            const int wb = q & 1;
-            tm_wait_st();  // the window of row q is in TMEM
-            const int4 cur = o;
-            // Fill row q + 1 (possibly in the next stage) into the other buffer.
-            if (q + 1 < nrows) {
-                if (++r == rows_in(st)) {
-                    r = 0;
-                    ++st;
-                    ++g;
-                    b = (int)(g % nst);
-                    if (!mbar_wait(full0 + 8 * b, (uint32_t)((g / nst) & 1))) {
-                        record(a.status, kDevTimeout);
-                        failed = true;
-                        break;
-                    }
-                    tb = atab + b * tab_stride;
-                }
-                o = *reinterpret_cast<const int4 *>(tb + r * dm_cta + kw);
-                fill(o, wb ^ 1);
-                if (r + 1 == rows_in(st)) {
-                    // every shared-memory read of this stage has been issued and
-                    // consumed by the TMEM stores: release it
-                    __syncwarp();
-                    if (lane == 0)
-                        mbar_arrive(empty0 + 8 * b);
-                }
+        for (;;) {
+            if (!mbar_spin(my_wfull + 8 * bq, ph)) {
+                record(a.status, kDevTimeout);
+                break;
             }
-            add_dm(0, wb, 0);
-            add_dm(1, wb, (cur.y - cur.x) / ELEM);
-            add_dm(2, wb, (cur.z - cur.x) / ELEM);
-            add_dm(3, wb, (cur.w - cur.x) / ELEM);
-            if (++since == kFloatBlock || q + 1 == nrows) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const RowMsg msg = my_msgs[bq];
+            if (msg.ctl & kMsgStop)
+                break;
+            const uint32_t tw = tm + (uint32_t)(kTmWin * bq);
+            {
+                uint64_t v[2][NP];
+                tm_ld18p(tw, v[0]);
+                tm_ld18p(tw + (uint32_t)msg.d1, v[1]);
+                tm_wait_ld();
+#pragma unroll
+                for (int jj = 0; jj < 2; ++jj)
+#pragma unroll
+                    for (int i = 0; i < NP; ++i) {
+                        reg_fence(v[jj][i]);
+                        fadd2p(P[jj][i], v[jj][i]);
+                    }
+                tm_ld18p(tw + (uint32_t)msg.d2, v[0]);
+                tm_ld18p(tw + (uint32_t)msg.d3, v[1]);
+                tm_wait_ld();
+#pragma unroll
+                for (int jj = 0; jj < 2; ++jj)
+#pragma unroll
+                    for (int i = 0; i < NP; ++i) {
+                        reg_fence(v[jj][i]);
+                        fadd2p(P[2 + jj][i], v[jj][i]);
+                    }
+            }
+            // the buffer's slices are in registers: hand it back
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncwarp();
+            if (lane == 0)
+                mbar_arrive(my_wempty + 8 * bq);
+            if (++bq == kTmBufs) {
+                bq = 0;
+                ph ^= 1u;
+            }
+            const bool last = (msg.ctl & kMsgLast) != 0;
+            if (++since == kFloatBlock || last) {
                 close_block(first_block);
                 first_block = false;
                 since = 0;
             }
+            if (last) {
+                store_tile(beam_at(a, msg.beam), msg.td * dm_cta + kw, msg.t0 + lane_t);
+                first_block = true;
+            }
         }
-        if (failed)
-            break;
-        store_tile(B, kthr, m0.t0 + lane_t);
-        ++g;  // the tile's last stage
-        (void)nstage;
     }
 
-    // Free TMEM once every consumer warp is done with it (also after a
+    // Free TMEM once every warp that touches it is done (also after a
     // timeout: every wait above is bounded).
+    tm_wait_st();
+    tm_wait_ld();
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    asm volatile("bar.sync 1, %0;" ::"n"(32 * kTmWarps) : "memory");
+    asm volatile("bar.sync 1, %0;" ::"n"(32 * (kTmThreadsWarps - 1)) : "memory");
     if (warp == 0) {
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tm_base),
                      "r"(kTmColsAlloc)
                      : "memory");
     }
-    (void)failed;
 }
 
 template <int ELEM>
@@ -664,7 +766,7 @@ cudaError_t launch_tm(const KArgs &a, unsigned grid, int threads, int smem, cuda
             return e;
         conf = smem;
     }
-    if (threads != 32 * (kTmWarps + 1))
+    if (threads != 32 * kTmThreadsWarps)
         return cudaErrorInvalidValue;
     k<<<grid, threads, smem, s>>>(a);
     return cudaGetLastError();

@@ -66,7 +66,7 @@ std::vector<dd_tiles> auto_tiles(dd_dtype t) {
         // TMEM-window shapes first (they need every 4-DM group's shift spread
         // to fit a window buffer), then the lane-interleaved ones.
         const int nw = t == DD_F16 ? 9 : 17;
-        for (int dw : {4, 2, 8, 1})
+        for (int dw : {kTmConsumerWarps, 2, 1})
             for (int cs : {16, 8, 4})
                 out.push_back(dd_tiles{4, dw, kTmConsumerWarps / dw, cs, nw});
     }
@@ -88,7 +88,7 @@ int64_t ring_smem(const Geometry &g, int64_t stage_bytes, int n) {
     return n * stage_bytes + table + n * (kStageMeta + rowinfo) + g.zero_bytes + 24 * (int64_t)n;
 }
 
-// Geometry of the TMEM-window kernel (FP16/FP32): 4 DMs per thread, 8
+// Geometry of the TMEM-window kernel (FP16/FP32): 4 DMs per thread, 4
 // consumer warps, samples per thread tm_samples(t); one staged copy per row
 // with room after it for the consumers' window reads; shared memory padded so
 // that only one CTA is resident per SM (each holds all 512 TMEM columns).
@@ -98,7 +98,7 @@ static dd_status make_geometry_tm(dd_plan_s *p, dd_dtype t, const dd_tiles &tl, 
     if (tl.dm_per_thread != 4 || tl.dm_warps < 1 || tl.time_warps < 1 ||
         tl.dm_warps * tl.time_warps != kTmConsumerWarps)
         return fail(DD_ERR_INVALID, "tile shape: the TMEM-window kernel takes dm_per_thread 4 "
-                                    "and dm_warps*time_warps = 8");
+                                    "and dm_warps*time_warps = 4");
     if (tl.chan_per_stage < 4 || tl.chan_per_stage > kFloatBlock || (tl.chan_per_stage & 3))
         return fail(DD_ERR_INVALID, "tile shape: chan_per_stage must be a multiple of 4, 4..64");
     Geometry r;
@@ -139,7 +139,7 @@ static dd_status make_geometry_tm(dd_plan_s *p, dd_dtype t, const dd_tiles &tl, 
                                         "); use words_per_thread 4 or 8");
     const int64_t wp = widest + (int64_t)r.elem * kTmWindow + 16 + 16;
     const int64_t stage_bytes = (int64_t)tl.chan_per_stage * wp;
-    r.zero_bytes = 16;  // the TMEM address slot
+    r.zero_bytes = 1280;  // window hand-off barriers, row messages, the TMEM address slot
     auto smem_for = [&](int64_t n) { return ring_smem(r, stage_bytes, (int)n); };
     int nst = 4;
     while (nst > 2 && smem_for(nst) > kMaxSmem)
@@ -156,7 +156,7 @@ static dd_status make_geometry_tm(dd_plan_s *p, dd_dtype t, const dd_tiles &tl, 
     r.nstages = nst;
     r.smem = (int)smem;
     r.builders = 0;
-    r.threads = 32 * (kTmConsumerWarps + 1);
+    r.threads = 32 * (2 * kTmConsumerWarps + 1);  // consumers, fillers, producer
     *g = r;
     return DD_OK;
 }

@@ -277,11 +277,11 @@ def test_tmem_window_shapes_are_chosen_only_where_the_spread_fits(dd):
     wide = dd.Plan(1024, 1500.0, -0.29296875, 64e-6, np.arange(0, 4096, 4, dtype=np.float32))
     assert wide.get_tiles("f32")[4] in (4, 8)
     with pytest.raises(dd.DDError) as e:
-        wide.set_tiles("f32", 4, 4, 2, 16, 17)
+        wide.set_tiles("f32", 4, 4, 1, 16, 17)
     assert "spread" in str(e.value)
     p = dd.Plan(64, 1500.0, -1.0, 64e-6, np.arange(32, dtype=np.float32))
-    for bad in [(2, 4, 2, 16, 17), (4, 4, 1, 16, 17), (4, 4, 2, 6, 17), (4, 4, 2, 16, 9)]:
+    for bad in [(2, 4, 1, 16, 17), (4, 4, 2, 16, 17), (4, 4, 1, 6, 17), (4, 4, 1, 16, 9)]:
         with pytest.raises(dd.DDError):
             p.set_tiles("f32", *bad)
     with pytest.raises(dd.DDError):
-        p.set_tiles("u8", 4, 4, 2, 16, 17)
+        p.set_tiles("u8", 4, 4, 1, 16, 17)

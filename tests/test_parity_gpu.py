@@ -172,14 +172,14 @@ def test_float_fuzz(dd, oracle_lib, kind, seed):
 
 
 TM_NW = {"f16": 9, "f32": 17}
-TILES_TM = [(4, 4, 2, 16), (4, 2, 4, 8), (4, 8, 1, 4), (4, 1, 8, 4), (4, 4, 2, 12)]
+TILES_TM = [(4, 4, 1, 16), (4, 4, 1, 8), (4, 2, 2, 8), (4, 1, 4, 4), (4, 4, 1, 12)]
 
 
 @pytest.mark.parametrize("tiles", TILES_TM)
 @pytest.mark.parametrize("kind", ["f32-frac", "f16-frac", "f32", "f16"])
 def test_tmem_kernel_fuzz(dd, oracle_lib, kind, tiles):
     """The TMEM-window kernel (4 DMs x 17 or 18 samples per thread, windows in
-    tensor memory) on ragged shapes: unsorted non-integer DMs, channel counts
+    tensor memory filled by their own warps) on ragged shapes: unsorted non-integer DMs, channel counts
     that are not multiples of a stage, block boundaries every 64 channels,
     ragged last time and DM tiles.  Integer-valued data must be exact; the
     rest within 1e-6 of sum |in| per cell."""
@@ -209,9 +209,9 @@ def test_tmem_kernel_degenerate_shapes(dd, oracle_lib, kind, nchan, ndm, nsamp_o
     rng = np.random.default_rng(nchan * 1000 + ndm * 10 + nsamp_out)
     band = (1400.0, -1.0, 1e-4)
     table = oracle_lib.dmshift(nchan, *band)
-    dms = rng.uniform(0.0, 20.0, size=ndm).astype(np.float32)
+    dms = rng.uniform(0.0, 8.0, size=ndm).astype(np.float32)   # spread fits the window
     plan = dd.Plan(nchan, *band, dms)
-    plan.set_tiles(kind[:3], 4, 4, 2, 8, TM_NW[kind[:3]])
+    plan.set_tiles(kind[:3], 4, 4, 1, 8, TM_NW[kind[:3]])
     nin = nsamp_out + plan.maxshift
     elem = 2 if kind.startswith("f16") else 4
     step = 16 // elem
