@@ -238,12 +238,6 @@ extern "C" dd_status dd_execute_host(dd_plan_t p, const void *in_host, dd_dtype 
 // Candidate tile shapes of the autotuner (validated later by make_geometry).
 static std::vector<dd_tiles> tune_candidates(dd_dtype t) {
     std::vector<dd_tiles> out;
-    if (t != DD_U8) {  // TMEM-window shapes (dd_kernel_tm.cuh)
-        const int nw = t == DD_F16 ? 9 : 17;
-        for (int dw : {1, 2, dd::kTmConsumerWarps})
-            for (int cs : {4, 8, 12, 16, 24, 32})
-                out.push_back(dd_tiles{4, dw, dd::kTmConsumerWarps / dw, cs, nw});
-    }
     const int dthrs[3] = {1, 2, 4};
     const int nws[2] = {8, 4};
     const int dws[8] = {4, 6, 8, 10, 12, 16, 20, 24};

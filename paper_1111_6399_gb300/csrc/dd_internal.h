@@ -58,17 +58,6 @@ DD_HD constexpr int max_consumer_warps(int dm_per_thread, int words) {
                       : (dm_per_thread >= 4 ? 20 : 24);
 }
 
-// FP16/FP32 tile shapes whose words_per_thread is 9 (FP16) or 17 (FP32) run
-// the TMEM-window kernel (dd_kernel_tm.cuh): 4 DMs x 18 or 17 consecutive
-// samples per thread, 4 consumer warps (dm_warps * time_warps = 4), each
-// 4-DM group's shift spread at most kTmWindow - samples per thread.
-constexpr int kTmConsumerWarps = 4;
-constexpr int kTmWindow = 72;
-inline bool tm_shape(dd_dtype t, const dd_tiles &tl) {
-    return (t == DD_F16 && tl.words_per_thread == 9) || (t == DD_F32 && tl.words_per_thread == 17);
-}
-inline int tm_samples(dd_dtype t) { return t == DD_F16 ? 18 : 17; }
-
 // Device status word values (written by kernels, read by dd_sync).
 constexpr int kDevOk = 0;
 constexpr int kDevTimeout = 1;

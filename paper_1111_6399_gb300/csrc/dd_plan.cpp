@@ -62,14 +62,6 @@ std::vector<dd_tiles> auto_tiles(dd_dtype t) {
     const dd_tiles base = default_tiles(t);
     const int max_t_cta = 4096;  // samples per CTA along time
     std::vector<dd_tiles> out;
-    if (t != DD_U8) {
-        // TMEM-window shapes first (they need every 4-DM group's shift spread
-        // to fit a window buffer), then the lane-interleaved ones.
-        const int nw = t == DD_F16 ? 9 : 17;
-        for (int dw : {kTmConsumerWarps, 2, 1})
-            for (int cs : {16, 8, 4})
-                out.push_back(dd_tiles{4, dw, kTmConsumerWarps / dw, cs, nw});
-    }
     for (int dcta = base.dm_per_thread * base.dm_warps; dcta >= 1; dcta /= 2) {
         const int dthr = std::min(base.dm_per_thread, dcta);
         const int wd = dcta / dthr;
@@ -88,79 +80,6 @@ int64_t ring_smem(const Geometry &g, int64_t stage_bytes, int n) {
     return n * stage_bytes + table + n * (kStageMeta + rowinfo) + g.zero_bytes + 24 * (int64_t)n;
 }
 
-// Geometry of the TMEM-window kernel (FP16/FP32): 4 DMs per thread, 4
-// consumer warps, samples per thread tm_samples(t); one staged copy per row
-// with room after it for the consumers' window reads; shared memory padded so
-// that only one CTA is resident per SM (each holds all 512 TMEM columns).
-static dd_status make_geometry_tm(dd_plan_s *p, dd_dtype t, const dd_tiles &tl, int d0, int nd,
-                                  Geometry *g) {
-    const int T = tm_samples(t);
-    if (tl.dm_per_thread != 4 || tl.dm_warps < 1 || tl.time_warps < 1 ||
-        tl.dm_warps * tl.time_warps != kTmConsumerWarps)
-        return fail(DD_ERR_INVALID, "tile shape: the TMEM-window kernel takes dm_per_thread 4 "
-                                    "and dm_warps*time_warps = 4");
-    if (tl.chan_per_stage < 4 || tl.chan_per_stage > kFloatBlock || (tl.chan_per_stage & 3))
-        return fail(DD_ERR_INVALID, "tile shape: chan_per_stage must be a multiple of 4, 4..64");
-    Geometry r;
-    r.tiles = tl;
-    r.elem = elem_size(t);
-    r.nph = 1;
-    r.span = 32 * T;
-    r.dm_cta = 4 * tl.dm_warps;
-    if (r.dm_cta > kMaxDmPerCta)
-        return fail(DD_ERR_INVALID, "tile shape: dm_per_thread*dm_warps must be <= 64");
-    r.t_cta = r.span * tl.time_warps;
-    r.ntile_d = (nd + r.dm_cta - 1) / r.dm_cta;
-    // DM k of the launch (from d0; past the plan's last DM the device list
-    // holds its largest DM).
-    auto dmv = [&](int64_t k) {
-        return p->dm_sorted[(size_t)std::min<int64_t>(d0 + k, (int64_t)p->ndm - 1)];
-    };
-    int64_t widest = 0, spread = 0;
-    for (int td = 0; td < r.ntile_d; ++td) {
-        const int64_t k0 = (int64_t)td * r.dm_cta;
-        const float dmin = dmv(k0), dmax = dmv(k0 + r.dm_cta - 1);
-        for (int c = 0; c < p->nchan; ++c) {
-            const float ds = p->dmshift[c];
-            const int64_t smin = trunc_product(dmin, ds);
-            const int64_t smax = trunc_product(dmax, ds);
-            const int64_t start = (r.elem * smin) & ~(int64_t)15;
-            const int64_t end = (int64_t)r.elem * (r.t_cta + smax);
-            widest = std::max(widest, (end - start + 15) & ~(int64_t)15);
-            for (int64_t k = k0; k < k0 + r.dm_cta; k += 4)
-                spread = std::max<int64_t>(spread, trunc_product(dmv(k + 3), ds) -
-                                                       trunc_product(dmv(k), ds));
-        }
-    }
-    if (spread > kTmWindow - T)
-        return fail(DD_ERR_INVALID, "tile shape: a 4-DM group's shift spread (" +
-                                        std::to_string(spread) + " samples) exceeds the "
-                                        "TMEM window (" + std::to_string(kTmWindow - T) +
-                                        "); use words_per_thread 4 or 8");
-    const int64_t wp = widest + (int64_t)r.elem * kTmWindow + 16 + 16;
-    const int64_t stage_bytes = (int64_t)tl.chan_per_stage * wp;
-    r.zero_bytes = 1280;  // window hand-off barriers, row messages, the TMEM address slot
-    auto smem_for = [&](int64_t n) { return ring_smem(r, stage_bytes, (int)n); };
-    int nst = 4;
-    while (nst > 2 && smem_for(nst) > kMaxSmem)
-        --nst;
-    int64_t smem = smem_for(nst);
-    if (smem > kMaxSmem)
-        return fail(DD_ERR_INVALID, "tile shape: staged window needs " + std::to_string(smem) +
-                                        " bytes of shared memory (limit 232448); use fewer "
-                                        "channels per stage or fewer DMs per CTA");
-    // Two resident CTAs would ask for 1024 TMEM columns: keep one per SM.
-    smem = std::max<int64_t>(smem, 116 * 1024);
-    r.wp = (int)wp;
-    r.stage_bytes = (int)stage_bytes;
-    r.nstages = nst;
-    r.smem = (int)smem;
-    r.builders = 0;
-    r.threads = 32 * (2 * kTmConsumerWarps + 1);  // consumers, fillers, producer
-    *g = r;
-    return DD_OK;
-}
-
 dd_status make_geometry(dd_plan_s *p, dd_dtype t, const dd_tiles &tl, Geometry *g) {
     return make_geometry_range(p, t, tl, 0, p->ndm, g);
 }
@@ -171,8 +90,6 @@ dd_status make_geometry_range(dd_plan_s *p, dd_dtype t, const dd_tiles &tl, int 
         return fail(DD_ERR_INVALID, "DM range outside the plan");
     if (!valid_dtype(t))
         return fail(DD_ERR_INVALID, "unknown dtype");
-    if (tm_shape(t, tl))
-        return make_geometry_tm(p, t, tl, d0, nd, g);
     const int dthr = tl.dm_per_thread;
     const int nw = tl.words_per_thread;
     bool ok_dthr = dthr == 1 || dthr == 2 || dthr == 4;

@@ -264,24 +264,3 @@ def test_channelise_validates_before_touching_a_gpu(dd):
     # fewer than M*T raw samples: no spectra, a no-op that needs no device
     assert dd.lib.dd_channelise(None, 252, 2, 63, 16, 4, None, 1, 0.5, None, 0, None) == 0
 
-
-def test_tmem_window_shapes_are_chosen_only_where_the_spread_fits(dd):
-    """FP16/FP32 plans pick the TMEM-window kernel (words_per_thread 9 / 17)
-    when every 4-DM group's shift spread fits its 72-column window, and fall
-    back to the lane-interleaved kernel otherwise; invalid TMEM shapes are
-    refused by the host checks."""
-    for w in (fb.LBAND, fb.LOWFREQ):
-        p = dd.Plan(w.nchan, w.fch1, w.foff, w.tsamp, w.dm_list())
-        assert p.get_tiles("f16")[4] == 9 and p.get_tiles("f32")[4] == 17
-        assert p.get_tiles("u8")[4] in (4, 8)
-    wide = dd.Plan(1024, 1500.0, -0.29296875, 64e-6, np.arange(0, 4096, 4, dtype=np.float32))
-    assert wide.get_tiles("f32")[4] in (4, 8)
-    with pytest.raises(dd.DDError) as e:
-        wide.set_tiles("f32", 4, 4, 1, 16, 17)
-    assert "spread" in str(e.value)
-    p = dd.Plan(64, 1500.0, -1.0, 64e-6, np.arange(32, dtype=np.float32))
-    for bad in [(2, 4, 1, 16, 17), (4, 4, 2, 16, 17), (4, 4, 1, 6, 17), (4, 4, 1, 16, 9)]:
-        with pytest.raises(dd.DDError):
-            p.set_tiles("f32", *bad)
-    with pytest.raises(dd.DDError):
-        p.set_tiles("u8", 4, 4, 1, 16, 17)

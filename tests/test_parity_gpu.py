@@ -171,57 +171,6 @@ def test_float_fuzz(dd, oracle_lib, kind, seed):
         assert np.array_equal(got.astype(np.float64), want)
 
 
-TM_NW = {"f16": 9, "f32": 17}
-TILES_TM = [(4, 4, 1, 16), (4, 4, 1, 8), (4, 2, 2, 8), (4, 1, 4, 4), (4, 4, 1, 12)]
-
-
-@pytest.mark.parametrize("tiles", TILES_TM)
-@pytest.mark.parametrize("kind", ["f32-frac", "f16-frac", "f32", "f16"])
-def test_tmem_kernel_fuzz(dd, oracle_lib, kind, tiles):
-    """The TMEM-window kernel (4 DMs x 17 or 18 samples per thread, windows in
-    tensor memory filled by their own warps) on ragged shapes: unsorted non-integer DMs, channel counts
-    that are not multiples of a stage, block boundaries every 64 channels,
-    ragged last time and DM tiles.  Integer-valued data must be exact; the
-    rest within 1e-6 of sum |in| per cell."""
-    rng = np.random.default_rng(sum(tiles) * 7 + len(kind))
-    nchan = int(rng.integers(60, 300))
-    ndm = int(rng.integers(5, 90))
-    nsamp_out = int(rng.integers(100, 6000))
-    full = (*tiles, TM_NW[kind[:3]])
-    plan, table, dms, nin, data = _case_that_fits(dd, rng, nchan, ndm, nsamp_out, kind, full,
-                                                  dm_hi=40.0)
-    assert plan.get_tiles(kind[:3]) == full
-    got = _run(dd, plan, data, nin, nsamp_out)
-    want, asum = oracle_lib.dedisperse(np.ascontiguousarray(data[:, :nin]), table, dms,
-                                       nsamp_out, with_abssum=True)
-    if kind.endswith("frac"):
-        _check_float(got, want, asum)
-    else:
-        assert np.array_equal(got.astype(np.float64), want)
-
-
-@pytest.mark.parametrize("kind", ["f32-frac", "f16-frac"])
-@pytest.mark.parametrize("nchan,ndm,nsamp_out", [(1, 1, 1), (2, 3, 17), (3, 4, 577), (5, 9, 1),
-                                                 (64, 4, 544), (65, 8, 1089), (129, 5, 2)])
-def test_tmem_kernel_degenerate_shapes(dd, oracle_lib, kind, nchan, ndm, nsamp_out):
-    """Single channel, single DM, single sample, one block of 64 channels and
-    one past it, outputs one sample past a warp's span."""
-    rng = np.random.default_rng(nchan * 1000 + ndm * 10 + nsamp_out)
-    band = (1400.0, -1.0, 1e-4)
-    table = oracle_lib.dmshift(nchan, *band)
-    dms = rng.uniform(0.0, 8.0, size=ndm).astype(np.float32)   # spread fits the window
-    plan = dd.Plan(nchan, *band, dms)
-    plan.set_tiles(kind[:3], 4, 4, 1, 8, TM_NW[kind[:3]])
-    nin = nsamp_out + plan.maxshift
-    elem = 2 if kind.startswith("f16") else 4
-    step = 16 // elem
-    data = fb.random_filterbank(rng, nchan, nin, kind, pitch=(nin + step - 1) // step * step)
-    got = _run(dd, plan, data, nin, nsamp_out)
-    want, asum = oracle_lib.dedisperse(np.ascontiguousarray(data[:, :nin]), table, dms,
-                                       nsamp_out, with_abssum=True)
-    _check_float(got, want, asum)
-
-
 def test_extreme_values_u8_4096_channels(dd, oracle_lib):
     """All-255 input over 4096 channels: the largest sums (1,044,480) are exact,
     including across the 256-channel SWAR widening."""
