@@ -456,9 +456,60 @@ def detect_section(dd, torch, out, w: fb.Workload, hbm_gbs: float, dms, reps: in
                                     "t": int(tpk[d, lev]), "snr": float(snr[d, lev])}}
 
 
+def fused_detect_section(dd, torch, dev, w: fb.Workload, reps: int = 10) -> dict:
+    """dd_execute_detect (the boxcar search fused into the de-dispersion
+    kernel) against dd_execute followed by dd_detect on the same beam and
+    plane, both timed with CUDA events over `reps` steps (inputs larger than
+    L2); the two give identical search results, which is checked."""
+    plan = dd.Plan(w.nchan, w.fch1, w.foff, w.tsamp, w.dm_list())
+    host, nin = beam_input(w, plan, "u8")
+    x = torch.from_numpy(host).to(dev)
+    out = torch.empty((w.ndm, w.nsamp_out), dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def fused():
+        return plan.execute_detect(x, out, nlevels=9, nsamp_in=nin, stream=stream)
+
+    def separate():
+        plan.execute(x, out, nsamp_in=nin, stream=stream)
+        return dd.detect(out, nlevels=9, integer_valued=True, stream=stream)
+
+    res = {}
+    for name, fn in (("fused", fused), ("separate", separate)):
+        for _ in range(3):
+            fn()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        n0 = dd.launch_count()
+        e0.record(stream)
+        for _ in range(reps):
+            r = fn()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        res[name] = {"ms": e0.elapsed_time(e1) / reps,
+                     "launches": (dd.launch_count() - n0) // reps,
+                     "result": [t.clone() for t in r]}
+    same = all(torch.equal(a, b) for a, b in zip(res["fused"]["result"],
+                                                 res["separate"]["result"]))
+    snr = res["fused"]["result"][2].cpu().numpy()
+    tpk = res["fused"]["result"][3].cpu().numpy()
+    d, lev = np.unravel_index(int(np.argmax(snr)), snr.shape)
+    out_d = {"workload": w.name, "tiles": plan.get_tiles("u8"),
+             "fused_ms": res["fused"]["ms"], "separate_ms": res["separate"]["ms"],
+             "fused_launches": res["fused"]["launches"],
+             "separate_launches": res["separate"]["launches"],
+             "saved_ms": res["separate"]["ms"] - res["fused"]["ms"],
+             "identical_results": bool(same),
+             "best": {"dm": float(w.dm_list()[d]), "width": 1 << int(lev), "t": int(tpk[d, lev]),
+                      "snr": float(snr[d, lev])}}
+    del x, out
+    torch.cuda.empty_cache()
+    return out_d
+
+
 def serving_section(dd, torch, dev, seconds: float = 8.0, speed: float = 1.25):
     """128 streaming L-band beams (1024 channels, 1024 DMs, blocks of 65536
-    samples = 4.194 s) served with continuous batching: Poisson arrivals at
+    samples = 4.194 s) served with continuous batching (the server's default
+    batching window, 1/64 of a block's duration): Poisson arrivals at
     `speed` x the aggregate real-time rate for `seconds`, then a saturating
     phase (blocks submitted as fast as the server accepts them)."""
     w = fb.LBAND
@@ -536,6 +587,9 @@ def serving_section(dd, torch, dev, seconds: float = 8.0, speed: float = 1.25):
     srv.close()
     sat_blocks = st["completed"] - done0
     adds_block = w.nchan * w.ndm * B
+
+    def gbs(nbytes, ms):
+        return nbytes / ms / 1e6 if ms > 0 else None
     return {"workload": "128 streaming beams x (1024 ch, 1024 DMs, 65536-sample blocks)",
             "arrivals": f"Poisson at {speed}x aggregate real time for {seconds:.0f} s",
             "blocks_real_time": st_rt["completed"], "busy_rejections": st_rt["rejected_busy"],
@@ -549,6 +603,15 @@ def serving_section(dd, torch, dev, seconds: float = 8.0, speed: float = 1.25):
             "saturated_mean_batch": sat_blocks / max(1, st["batches"] - st_rt["batches"]),
             "saturated_adds_per_s": sat_blocks * adds_block / wall_sat,
             "real_time_beams_sustained": sat_blocks / wall_sat * block_s,
+            "batch_window_ms": st_rt["batch_window_us"] / 1e3,
+            "copies": {"host_staging_gbs": gbs(st["staging_bytes"], st["staging_ms"]),
+                       "h2d_gbs": gbs(st["h2d_bytes"], st["h2d_ms"]),
+                       "d2h_gbs": gbs(st["d2h_bytes"], st["d2h_ms"]),
+                       "per_block_bytes": {"staging": w.nchan * B, "h2d": w.nchan * B,
+                                           "d2h": w.ndm * B * 4},
+                       "note": "host staging: dd_submit's copy into pinned memory (host "
+                               "threads, wall clock); h2d/d2h: device time of the batches' "
+                               "input and result copy phases"},
             "wall_s": wall_rt + wall_sat}
 
 
@@ -829,6 +892,9 @@ def run_ours(args, w):
     if world == 1 and not args.no_lband and w is not fb.LBAND:
         line["lband"] = beam_section(dd, torch, dev, fb.LBAND, "u8", max(3, min(args.steps, 100)),
                                      3, peak, nominal, args)
+    if not args.no_detect and world == 1:
+        line["fused_detect"] = {wl.name: fused_detect_section(dd, torch, dev, wl)
+                                for wl in (w, fb.LBAND) if wl.nsamp_out <= (1 << 21)}
     lb = fb.LBAND
     lb_nin = lb.nsamp_out + dd.Plan(lb.nchan, lb.fch1, lb.foff, lb.tsamp, lb.dm_list()).maxshift
     if not args.no_batch and world == 1:

@@ -202,6 +202,26 @@ dd_status dd_execute_noalloc(dd_plan_t plan, const void *in, dd_dtype dtype, int
  * dd_execute_noalloc cleared it. */
 dd_status dd_sync_noalloc(void *stream);
 
+/* De-disperse a uint8 beam like dd_execute and search the plane for pulses
+ * like dd_detect(plane, out_pitch, ndm, nsamp_out, nlevels, 1, ...), with the
+ * search fused into the de-dispersion kernel: each CTA searches the tile of
+ * the plane it has just finished while the tile is in L2, instead of a
+ * second pass reading the whole plane back from HBM (Sec. 4 / Fig. 3 find the
+ * pulse at its DM and time after the search).  The plane is still written to
+ * out.  Results are those of dd_detect on the same plane, bit for bit: per
+ * output row (caller's DM order) mean[ndm], std_out[ndm] and per (row,
+ * level) snr[ndm][nlevels], t_peak[ndm][nlevels] (device arrays, 8-byte
+ * aligned).  uint8 input only (integer planes), nlevels 1..9, 1 <= nsamp_out
+ * <= 2^21.  Uses one launch (no remainder-DM split) with 1024-sample tiles
+ * of 4 DMs x 8 words per thread: the plan's uint8 tile shape when it is one
+ * of those, else the first automatic shape that is.  Holds one int of device
+ * memory per tile, allocated with the plan on first use.  Asynchronous on
+ * stream; DD_ERR_INVALID (nothing launched) for bad arguments. */
+dd_status dd_execute_detect(dd_plan_t plan, const void *in, dd_dtype dtype, int64_t in_pitch,
+                            int64_t nsamp_in, float *out, int64_t out_pitch, int64_t nsamp_out,
+                            int nlevels, double *mean, double *std_out, double *snr,
+                            int64_t *t_peak, void *stream);
+
 /* --- input side: corner turn and bit unpacking ---------------------------- */
 
 /* Turn a block of filterbank spectra into the channel rows that dd_execute
@@ -396,6 +416,14 @@ typedef struct dd_server_stats {
     double mean_batch;       /* mean blocks per batched launch                  */
     int slots;               /* device slots (blocks in flight at most)         */
     int64_t device_bytes;    /* device memory held (slots + beam tails)         */
+    int64_t staging_bytes;   /* block bytes copied into pinned staging by dd_submit */
+    double staging_ms;       /* host time of those copies (wall clock, summed)  */
+    int64_t h2d_bytes;       /* block bytes copied host -> device               */
+    double h2d_ms;           /* device time of the batches' input phases (the    */
+                             /* host-to-device copies and the tail copies)      */
+    int64_t d2h_bytes;       /* result bytes copied device -> host              */
+    double d2h_ms;           /* device time of the batches' result copies        */
+    int64_t batch_window_us; /* batching window in force                        */
 } dd_server_stats;
 
 /* A server de-disperses streams of blocks from many beams (the real-time
@@ -409,7 +437,11 @@ typedef struct dd_server_stats {
  * batching.  Device memory = slots + tails, bounded by hbm_budget_bytes; the
  * number of slots is min(max_inflight, what the budget allows after tails).
  * Blocks wait in pinned host staging (2 x slots buffers); dd_submit returns
- * DD_ERR_BUSY when none is free. */
+ * DD_ERR_BUSY when none is free.  dd_submit copies a block into staging
+ * with a few host threads.  A partly filled batch waits up to the batching
+ * window for more ready blocks; unless set with dd_server_set_batch_window,
+ * the window is 1/64 of the shortest block duration of the server's beams
+ * (B * tsamp), at most 100 ms -- 65 ms for blocks of 65536 samples of 64 us. */
 dd_status dd_server_create(size_t hbm_budget_bytes, int max_inflight, dd_dtype dtype,
                            dd_server_t *server_out);
 

@@ -33,6 +33,7 @@ EXPORTS = [
     "dd_selftest_wait_timeout", "dd_server_set_batch_window", "dd_unpack", "dd_detect",
     "dd_frontend", "dd_frontend_work_bytes", "dd_channelise", "dd_channelise_nspec",
     "dd_pfb_prototype", "dd_sync_noalloc", "dd_selftest_noalloc_timeout", "dd_add_peak",
+    "dd_execute_detect",
 ]
 
 
@@ -57,7 +58,11 @@ class ServerStats(ctypes.Structure):
                 ("rejected_busy", ctypes.c_int64), ("batches", ctypes.c_int64),
                 ("p50_ms", ctypes.c_double), ("p99_ms", ctypes.c_double),
                 ("max_ms", ctypes.c_double), ("mean_batch", ctypes.c_double),
-                ("slots", ctypes.c_int), ("device_bytes", ctypes.c_int64)]
+                ("slots", ctypes.c_int), ("device_bytes", ctypes.c_int64),
+                ("staging_bytes", ctypes.c_int64), ("staging_ms", ctypes.c_double),
+                ("h2d_bytes", ctypes.c_int64), ("h2d_ms", ctypes.c_double),
+                ("d2h_bytes", ctypes.c_int64), ("d2h_ms", ctypes.c_double),
+                ("batch_window_us", ctypes.c_int64)]
 
     def as_dict(self):
         return {n: getattr(self, n) for n, _ in self._fields_}
@@ -88,6 +93,7 @@ def _load() -> ctypes.CDLL:
         "dd_execute_noalloc": (i32, [p, p, i32, i64, i64, p, i64, i64, p]),
         "dd_sync": (i32, [p, p]),
         "dd_sync_noalloc": (i32, [p]),
+        "dd_execute_detect": (i32, [p, p, i32, i64, i64, p, i64, i64, i32, p, p, p, p, p]),
         "dd_add_peak": (i32, [i32, i32, p, ctypes.POINTER(ctypes.c_double),
                               ctypes.POINTER(ctypes.c_double)]),
         "dd_selftest_noalloc_timeout": (i32, [i64, p]),
@@ -403,6 +409,35 @@ class Plan:
         check(lib.dd_execute_noalloc(self.handle, ctypes.c_void_p(in_ptr), dtype, in_pitch,
                                      nsamp_in, ctypes.c_void_p(out_ptr), out_pitch, nsamp_out,
                                      ctypes.c_void_p(stream)))
+
+    def execute_detect(self, inp, out, nlevels: int = 9, nsamp_in: int | None = None,
+                       nsamp_out: int | None = None, stream=None):
+        """dd_execute_detect on torch CUDA tensors: inp uint8 [nchan][pitch], out
+        float32 [ndm][pitch] (the plane, written as by execute).  Returns CUDA
+        tensors (mean[ndm], std[ndm], snr[ndm][nlevels], t[ndm][nlevels]) of the
+        fused boxcar search.  Asynchronous on stream."""
+        import torch
+        if not (inp.is_cuda and out.is_cuda) or inp.dim() != 2 or out.dim() != 2 \
+                or inp.stride(1) != 1 or out.stride(1) != 1 or out.dtype != torch.float32:
+            raise ValueError("inp/out must be 2-D CUDA tensors with contiguous rows; out float32")
+        nsamp_in = inp.shape[1] if nsamp_in is None else nsamp_in
+        nsamp_out = out.shape[1] if nsamp_out is None else nsamp_out
+        dev = out.device
+        ndm = self.ndm
+        mean = torch.empty(ndm, dtype=torch.float64, device=dev)
+        std = torch.empty(ndm, dtype=torch.float64, device=dev)
+        snr = torch.empty((ndm, nlevels), dtype=torch.float64, device=dev)
+        tpk = torch.empty((ndm, nlevels), dtype=torch.int64, device=dev)
+        s = torch.cuda.current_stream(dev) if stream is None else stream
+        check(lib.dd_execute_detect(self.handle, ctypes.c_void_p(inp.data_ptr()),
+                                    dtype_code(inp.dtype), inp.stride(0), nsamp_in,
+                                    ctypes.c_void_p(out.data_ptr()), out.stride(0), nsamp_out,
+                                    int(nlevels), ctypes.c_void_p(mean.data_ptr()),
+                                    ctypes.c_void_p(std.data_ptr()),
+                                    ctypes.c_void_p(snr.data_ptr()),
+                                    ctypes.c_void_p(tpk.data_ptr()),
+                                    ctypes.c_void_p(s.cuda_stream)))
+        return mean, std, snr, tpk
 
     @staticmethod
     def sync_noalloc(stream: int = 0) -> None:

@@ -235,6 +235,91 @@ extern "C" dd_status dd_execute_host(dd_plan_t p, const void *in_host, dd_dtype 
     return dd_sync(p, nullptr);
 }
 
+// De-dispersion of a uint8 beam with the boxcar search of dd_detect fused
+// into the kernel's epilogue: the plane is written to out as by dd_execute,
+// and each CTA searches the tile it has just finished while it is in L2.
+extern "C" dd_status dd_execute_detect(dd_plan_t p, const void *in, dd_dtype dtype,
+                                       int64_t in_pitch, int64_t nsamp_in, float *out,
+                                       int64_t out_pitch, int64_t nsamp_out, int nlevels,
+                                       double *mean, double *std_out, double *snr,
+                                       int64_t *t_peak, void *stream) {
+    dd::Range nvtx_range("dd_execute_detect");
+    if (!p)
+        return fail(DD_ERR_INVALID, "plan is NULL");
+    if (dtype != DD_U8)
+        return fail(DD_ERR_INVALID, "fused detection takes uint8 input (integer planes)");
+    dd_status st = check_layout(p, dtype, in_pitch, nsamp_in, out_pitch, nsamp_out, true);
+    if (st != DD_OK)
+        return st;
+    if (nlevels < 1 || nlevels > 9)
+        return fail(DD_ERR_INVALID, "nlevels must be 1..9 (boxcar widths up to 256)");
+    if (nsamp_out < 1 || nsamp_out > (1LL << 21))
+        return fail(DD_ERR_INVALID, "nsamp_out must be 1 .. 2^21 for an integer search");
+    if (!in || !out || !aligned16(in) || !aligned16(out))
+        return fail(DD_ERR_INVALID, "in and out must be non-NULL and 16-byte aligned");
+    if (!mean || !std_out || !snr || !t_peak || ((uintptr_t)mean & 7u) ||
+        ((uintptr_t)std_out & 7u) || ((uintptr_t)snr & 7u) || ((uintptr_t)t_peak & 7u))
+        return fail(DD_ERR_INVALID, "NULL or misaligned detection output");
+    // Tile shape: the plan's uint8 shape if it has 1024-sample tiles of 4 DMs
+    // x 8 words per thread, else the first automatic shape that does.
+    dd::Geometry g;
+    if ((st = dd::plan_geometry(p, dtype, &g)) != DD_OK)
+        return st;
+    auto fits = [](const dd::Geometry &x) {
+        return x.tiles.dm_per_thread == 4 && x.tiles.words_per_thread == 8 &&
+               x.tiles.time_warps == 1 && x.t_cta == 1024;
+    };
+    if (!fits(g)) {
+        bool found = false;
+        for (const dd_tiles &cand : dd::auto_tiles(dtype)) {
+            dd_tiles t = cand;
+            t.time_warps = 1;
+            if (t.dm_per_thread == 4 && t.words_per_thread == 8 &&
+                dd::make_geometry(p, dtype, t, &g) == DD_OK && fits(g)) {
+                found = true;
+                break;
+            }
+        }
+        if (!found)
+            return fail(DD_ERR_INVALID, "no 1024-sample tile shape fits this plan for fused "
+                                        "detection");
+    }
+    dd::DevTables *dt = nullptr;
+    if ((st = dd::device_tables(p, &dt)) != DD_OK)
+        return st;
+    const int64_t ntile_t = (nsamp_out + g.t_cta - 1) / g.t_cta;
+    const int64_t ncnt = ntile_t * g.ntile_d;
+    {
+        std::lock_guard<std::mutex> lk(p->mu);
+        if (dt->det_cnt_n < ncnt) {
+            cudaFree(dt->det_cnt);
+            dt->det_cnt = nullptr;
+            dt->det_cnt_n = 0;
+            if (cudaMalloc((void **)&dt->det_cnt, sizeof(int) * (size_t)ncnt) != cudaSuccess) {
+                cudaGetLastError();
+                return fail(DD_ERR_NOMEM, "detection counter allocation failed");
+            }
+            dt->det_cnt_n = ncnt;
+        }
+    }
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaMemsetAsync(dt->det_cnt, 0, sizeof(int) * (size_t)ncnt, s);
+    if (e != cudaSuccess)
+        return fail(DD_ERR_CUDA, std::string("counter memset: ") + cudaGetErrorString(e));
+    if ((st = dd::detect_begin(p->ndm, nlevels, mean, std_out, snr, s)) != DD_OK)
+        return st;
+    dd::DetectTargets det;
+    det.nlevels = nlevels;
+    det.mean = mean;
+    det.sd = std_out;
+    det.snr = snr;
+    det.tpk = t_peak;
+    if ((st = dd::launch_dedisperse_detect(p, g, *dt, in, in_pitch, nsamp_in, out, out_pitch,
+                                           nsamp_out, det, dt->det_cnt, stream)) != DD_OK)
+        return st;
+    return dd::detect_finalize_int(p->ndm, nsamp_out, nlevels, mean, std_out, snr, t_peak, s);
+}
+
 // Candidate tile shapes of the autotuner (validated later by make_geometry).
 static std::vector<dd_tiles> tune_candidates(dd_dtype t) {
     std::vector<dd_tiles> out;

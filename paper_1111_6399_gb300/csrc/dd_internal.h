@@ -2,6 +2,8 @@
 // translation units of libdd.  Not part of the public ABI (include/dd.h).
 #pragma once
 
+#include <cuda_runtime_api.h>
+
 #include <cstdint>
 #include <map>
 #include <mutex>
@@ -69,6 +71,16 @@ struct DevTables {
     int *perm = nullptr;         // [ndm_pad]: output row of sorted DM k, -1 for padding
     int *status = nullptr;       // device status word
     int ndm_pad = 0;
+    int *det_cnt = nullptr;      // tile-boundary counters of fused detection
+    int64_t det_cnt_n = 0;
+};
+
+// Accumulators of a boxcar search (dd_detect, dd_execute_detect): caller-owned
+// output arrays, used as exact sums and keys until the finalize step.
+struct DetectTargets {
+    int nlevels = 0;
+    double *mean = nullptr, *sd = nullptr, *snr = nullptr;
+    int64_t *tpk = nullptr;
 };
 
 // Launch geometry derived from a tile shape and the plan's tables.
@@ -114,7 +126,8 @@ dd_status fail(dd_status st, const std::string &msg);
 // Dynamic shared memory of a ring of n stages of stage_bytes each for a
 // geometry: the stages, the offset table, the stage records, the per-row
 // byte counts (with phases to build), the zero row and three mbarriers per
-// stage, in the order the kernel lays them out.
+// stage, in the order the kernel lays them out, and 16 bytes for the
+// epilogue of fused detection.
 int64_t ring_smem(const Geometry &g, int64_t stage_bytes, int n);
 
 // Host checks of a beam's layout shared by the entry points that run one
@@ -166,5 +179,21 @@ dd_status launch_dedisperse(dd_plan_s *p, const Geometry &g, const DevTables &dt
                             bool split_tail = true);
 
 void count_launch(int n = 1);
+
+// Boxcar search accumulators: clear them (dd_detect.cu), and turn them into
+// mean, std, S/N and peak t for an integer-valued plane.
+dd_status detect_begin(int ndm, int nlevels, double *mean, double *sd, double *snr,
+                       cudaStream_t s);
+dd_status detect_finalize_int(int ndm, int64_t nsamp, int nlevels, double *mean, double *sd,
+                              double *snr, int64_t *tpk, cudaStream_t s);
+
+// One uint8 de-dispersion launch (no remainder split) with the boxcar search
+// fused into its epilogue (dd_launch.cpp): g must have 4 DMs x 8 words per
+// thread and one time warp (1024-sample tiles); det_cnt holds
+// g.ntile_d * ntile_t zeroed ints.
+dd_status launch_dedisperse_detect(dd_plan_s *p, const Geometry &g, const DevTables &dt,
+                                   const void *in, int64_t in_pitch, int64_t nsamp_in,
+                                   float *out, int64_t out_pitch, int64_t nsamp_out,
+                                   const DetectTargets &det, int *det_cnt, void *stream);
 
 }  // namespace dd

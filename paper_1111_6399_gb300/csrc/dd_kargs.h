@@ -43,6 +43,16 @@ struct KArgs {
     uint32_t one;           // the constant 1, opaque to the compiler
     int builders;           // phase-builder warps (8/16-bit input; 0 for FP32)
     int *status;
+    // Detection fused into the epilogue (uint8 single-beam launches with
+    // 1024-sample time tiles; det_s1 == NULL: off): per output row the exact
+    // sums S1, S2 and per (row, level) the packed boxcar keys, as dd_detect
+    // accumulates them; det_cnt: one counter per (DM tile, time tile),
+    // zeroed before the launch, deciding which tile of a neighbouring pair
+    // searches the boxcar starts across their boundary.
+    unsigned long long *det_s1, *det_s2, *det_keys;
+    int *det_cnt;
+    int det_nlevels;
+    int det_ntile_t;
 };
 
 // Launch dedisperse_kernel<elem, dthr, nw> with `threads` threads per CTA.

@@ -53,6 +53,7 @@
 #include <algorithm>
 #include <cstdint>
 
+#include "dd_detect_seg.cuh"
 #include "dd_kargs.h"
 #include "dd_internal.h"
 
@@ -223,11 +224,89 @@ __device__ __forceinline__ int beam_of_tile(const KArgs &a, int64_t tile) {
 }
 
 // ---------------------------------------------------------------------------
+// Fused detection: the boxcar search of dd_detect run on a finished tile of
+// the plane (DMs kcta .. kcta + dm_cta - 1, samples t0 .. t0 + 1023) by the
+// consumer warps of the CTA that computed it, reading the tile back from L2.
+// Boxcar start positions are split so that each is searched once:
+//   * [t0, t0 + 768) by tile k itself (every window ends inside the tile);
+//   * [t0 - 256, t0) -- windows across the boundary with tile k - 1 -- by
+//     whichever of the two tiles finishes second (an atomic counter per
+//     boundary: the tile that finds it at 1 searches it; both tiles' values
+//     are then final and visible);
+//   * the last tile of a row searches [t0, nsamp) whole.
+// The sums S1, S2 of the searched positions' samples and the keys go to the
+// same accumulators as dd_detect's, so its finalize step completes the
+// search.  Returns false if a bounded wait ran out (recorded).
+// ---------------------------------------------------------------------------
+__device__ __noinline__ bool detect_epilogue(const KArgs &a, int td, int64_t t0, int dm_cta,
+                                             int t_cta, int ncw, int warp, int lane, int tid,
+                                             uint32_t ep_bar, int *ep_flags) {
+    const BeamArgs &B = a.beam0;
+    // Every consumer's stores and reductions of the tile are visible before
+    // the counters or any search read them.
+    __threadfence();
+    __syncwarp();
+    if (lane == 0)
+        mbar_arrive(ep_bar);
+    if (!mbar_wait(ep_bar, 0)) {
+        record(a.status, kDevTimeout);
+        return false;
+    }
+    const int K = a.det_ntile_t;
+    const int k = (int)(t0 / t_cta);
+    if (tid == 0) {
+        int *cnt = a.det_cnt + (int64_t)td * K;
+        __threadfence();
+        const int left = k > 0 ? (atomicAdd(&cnt[k], 1) == 1) : 0;
+        const int right = k + 1 < K ? (atomicAdd(&cnt[k + 1], 1) == 1) : 0;
+        __threadfence();
+        ep_flags[0] = left;
+        ep_flags[1] = right;
+    }
+    __syncwarp();
+    if (lane == 0)
+        mbar_arrive(ep_bar);
+    if (!mbar_wait(ep_bar, 1)) {
+        record(a.status, kDevTimeout);
+        return false;
+    }
+    const bool left = ep_flags[0] != 0, right = ep_flags[1] != 0;
+    const int64_t n = B.nsamp_out;
+    const int nl = a.det_nlevels;
+    for (int it = warp; it < 3 * dm_cta; it += ncw) {
+        const int j = it / 3, part = it % 3;
+        const int row = B.perm[td * dm_cta + j];
+        if (row < 0 || (part == 1 && !left) || (part == 2 && !right))
+            continue;
+        const float *x = B.out + (int64_t)row * B.out_pitch;
+        if (part == 0 && k + 1 == K) {
+            detect_segment<true, true, 32, true>(x, n, t0, row, nl, lane, a.one, a.det_s1,
+                                                 a.det_s2, a.det_keys);
+        } else if (part == 0) {
+            // loads reach 32 * (24 + kReach) samples from t0
+            if (t0 + 32 * (24 + kReach) <= n)
+                detect_segment<true, false, 24, true>(x, n, t0, row, nl, lane, a.one, a.det_s1,
+                                                      a.det_s2, a.det_keys);
+            else
+                detect_segment<true, true, 24, true>(x, n, t0, row, nl, lane, a.one, a.det_s1,
+                                                     a.det_s2, a.det_keys);
+        } else {
+            const int64_t s0 = part == 1 ? t0 - 256 : t0 + 768;
+            detect_segment<true, true, 8, true>(x, n, s0, row, nl, lane, a.one, a.det_s1,
+                                                a.det_s2, a.det_keys);
+        }
+    }
+    return true;
+}
+
+// ---------------------------------------------------------------------------
 // The de-dispersion kernel.  ELEM = bytes per sample (1, 2, 4); DT = DMs per
 // consumer thread; NW = 4-byte words per DM per consumer thread (4 or 8).
 // Warps 0..ncw-1 consume, warp ncw produces, warps ncw+1.. build phases.
 // ---------------------------------------------------------------------------
-template <int ELEM, int DT, int NW>
+// DET: the uint8 form that also searches the finished plane for pulses
+// (fused detection, see detect_epilogue below).
+template <int ELEM, int DT, int NW, bool DET = false>
 __global__ void __launch_bounds__(32 * (max_consumer_warps(DT, NW) + 1 + (ELEM < 4 ? kMaxBuilders : 0)), 1)
     dedisperse_kernel(const __grid_constant__ KArgs a) {
     constexpr int NPH = 4 / ELEM;            // phase copies per row
@@ -259,6 +338,9 @@ __global__ void __launch_bounds__(32 * (max_consumer_warps(DT, NW) + 1 + (ELEM <
     const uint32_t full0 = smem_addr(&mbar[0]);
     const uint32_t empty0 = smem_addr(&mbar[nst]);
     const uint32_t raw0 = smem_addr(&mbar[2 * nst]);
+    // Fused detection: a barrier of the consumer warps and two flags.
+    const uint32_t ep_bar = smem_addr(&mbar[3 * nst]);
+    int *ep_flags = reinterpret_cast<int *>(&mbar[3 * nst + 1]);
     // The producer hands a stage to the builders (raw) or, without phases to
     // build, straight to the consumers (full).
     const uint32_t hand0 = BUILD ? raw0 : full0;
@@ -273,6 +355,8 @@ __global__ void __launch_bounds__(32 * (max_consumer_warps(DT, NW) + 1 + (ELEM <
             mbar_init(empty0 + 8 * b, ncw);
             mbar_init(raw0 + 8 * b, 1);
         }
+        if (DET)
+            mbar_init(ep_bar, ncw);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
@@ -549,6 +633,8 @@ __global__ void __launch_bounds__(32 * (max_consumer_warps(DT, NW) + 1 + (ELEM <
     // Current tile (from the stage records).
     int beam = 0, kthr = 0;
     int64_t tw = 0;
+    int tile_td = 0;
+    int64_t tile_t0 = 0;
     int since_flush = 0;
     bool flushed_once = false;
 
@@ -745,6 +831,8 @@ __global__ void __launch_bounds__(32 * (max_consumer_warps(DT, NW) + 1 + (ELEM <
             beam = m.beam;
             kthr = m.td * dm_cta + kw;
             tw = m.t0 + (int64_t)wti * SPAN;
+            tile_td = m.td;
+            tile_t0 = m.t0;
             since_flush = 0;
             flushed_once = false;
         }
@@ -817,13 +905,18 @@ __global__ void __launch_bounds__(32 * (max_consumer_warps(DT, NW) + 1 + (ELEM <
                 block_float();
                 store_float();
             }
+            if constexpr (DET) {
+                if (!detect_epilogue(a, tile_td, tile_t0, dm_cta, t_cta, ncw, warp, lane, tid,
+                                     ep_bar, ep_flags))
+                    return;
+            }
         }
     }
 }
 
-template <int ELEM, int DT, int NW>
+template <int ELEM, int DT, int NW, bool DET = false>
 cudaError_t launch_one(const KArgs &a, unsigned grid, int threads, int smem, cudaStream_t s) {
-    auto k = dedisperse_kernel<ELEM, DT, NW>;
+    auto k = dedisperse_kernel<ELEM, DT, NW, DET>;
     // Raise the dynamic shared-memory limit only when a launch needs more than
     // before (so a launch inside a stream capture never changes attributes
     // after an eager launch of the same shape).
@@ -845,6 +938,13 @@ cudaError_t launch_one(const KArgs &a, unsigned grid, int threads, int smem, cud
 template <int ELEM>
 cudaError_t launch_elem(const KArgs &a, unsigned grid, int threads, int smem, cudaStream_t s,
                         int dthr, int nw) {
+    if constexpr (ELEM == 1) {
+        if (a.det_s1) {  // fused detection: uint8, 4 DMs x 8 words per thread
+            if (nw != 8 || dthr != 4)
+                return cudaErrorInvalidValue;
+            return launch_one<1, 4, 8, true>(a, grid, threads, smem, s);
+        }
+    }
     if (nw == 4) {
         switch (dthr) {
         case 1: return launch_one<ELEM, 1, 4>(a, grid, threads, smem, s);

@@ -91,7 +91,8 @@ bool split_pays(const Geometry &g, const Geometry &gt, int64_t ntile_t, int64_t 
 // d0 on.
 cudaError_t enqueue(dd_plan_s *p, const Geometry &g, const DevTables &dt, int d0, int ntile_d,
                     const void *in, dd_dtype dtype, int64_t in_pitch, int64_t nsamp_in,
-                    float *out, int64_t out_pitch, int64_t nsamp_out, cudaStream_t s) {
+                    float *out, int64_t out_pitch, int64_t nsamp_out, cudaStream_t s,
+                    const DetectTargets *det = nullptr, int *det_cnt = nullptr) {
     KArgs a{};
     BeamArgs &b = a.beam0;
     b.in = static_cast<const uint8_t *>(in);
@@ -121,6 +122,14 @@ cudaError_t enqueue(dd_plan_s *p, const Geometry &g, const DevTables &dt, int d0
     a.status = dt.status;
     const int64_t ntile_t = (nsamp_out + g.t_cta - 1) / g.t_cta;
     a.total_tiles = ntile_t * ntile_d;
+    if (det) {
+        a.det_s1 = reinterpret_cast<unsigned long long *>(det->mean);
+        a.det_s2 = reinterpret_cast<unsigned long long *>(det->sd);
+        a.det_keys = reinterpret_cast<unsigned long long *>(det->snr);
+        a.det_cnt = det_cnt;
+        a.det_nlevels = det->nlevels;
+        a.det_ntile_t = (int)ntile_t;
+    }
     const unsigned grid = (unsigned)a.total_tiles;
     const int dthr = g.tiles.dm_per_thread, nw = g.tiles.words_per_thread;
     switch (dtype) {
@@ -132,6 +141,27 @@ cudaError_t enqueue(dd_plan_s *p, const Geometry &g, const DevTables &dt, int d0
 }
 
 }  // namespace
+
+dd_status launch_dedisperse_detect(dd_plan_s *p, const Geometry &g, const DevTables &dt,
+                                   const void *in, int64_t in_pitch, int64_t nsamp_in,
+                                   float *out, int64_t out_pitch, int64_t nsamp_out,
+                                   const DetectTargets &det, int *det_cnt, void *stream) {
+    if (g.tiles.dm_per_thread != 4 || g.tiles.words_per_thread != 8 || g.tiles.time_warps != 1 ||
+        g.t_cta != 1024)
+        return fail(DD_ERR_INVALID, "fused detection needs 4 DMs x 8 words per thread and one "
+                                    "time warp (1024-sample tiles)");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (g_prof_start)
+        cudaEventRecord(g_prof_start, s);
+    const cudaError_t e = enqueue(p, g, dt, 0, g.ntile_d, in, DD_U8, in_pitch, nsamp_in, out,
+                                  out_pitch, nsamp_out, s, &det, det_cnt);
+    if (e != cudaSuccess)
+        return fail(DD_ERR_CUDA, std::string("kernel launch failed: ") + cudaGetErrorString(e));
+    if (g_prof_stop)
+        cudaEventRecord(g_prof_stop, s);
+    count_launch(1);
+    return DD_OK;
+}
 
 dd_status launch_dedisperse(dd_plan_s *p, const Geometry &g, const DevTables &dt, const void *in,
                             dd_dtype dtype, int64_t in_pitch, int64_t nsamp_in, float *out,

@@ -77,7 +77,9 @@ std::vector<dd_tiles> auto_tiles(dd_dtype t) {
 int64_t ring_smem(const Geometry &g, int64_t stage_bytes, int n) {
     const int64_t table = ((int64_t)n * g.tiles.chan_per_stage * g.dm_cta * 4 + 15) / 16 * 16;
     const int64_t rowinfo = g.nph > 1 ? kRowInfoBytes : 0;
-    return n * stage_bytes + table + n * (kStageMeta + rowinfo) + g.zero_bytes + 24 * (int64_t)n;
+    // + 16: the epilogue barrier and flags of fused detection
+    return n * stage_bytes + table + n * (kStageMeta + rowinfo) + g.zero_bytes + 24 * (int64_t)n +
+           16;
 }
 
 dd_status make_geometry(dd_plan_s *p, dd_dtype t, const dd_tiles &tl, Geometry *g) {
@@ -368,6 +370,7 @@ void dd_plan_destroy(dd_plan_t p) {
         cudaFree(kv.second.dm_sorted);
         cudaFree(kv.second.perm);
         cudaFree(kv.second.status);
+        cudaFree(kv.second.det_cnt);
     }
     if (cur >= 0 && !p->dev.empty())
         cudaSetDevice(cur);

@@ -76,7 +76,88 @@ struct Lane {  // launch resources of one of the two alternating streams
     dd::BeamArgs *h_desc = nullptr;  // pinned
     int *d_counter = nullptr;
     cudaEvent_t done = nullptr;
+    // Timing of the last batch on this lane: input copies [t0, t1), kernel
+    // [t1, t2), result copies [t2, t3); read when the lane is reused.
+    cudaEvent_t t[4] = {nullptr, nullptr, nullptr, nullptr};
+    int64_t h2d_bytes = 0, d2h_bytes = 0;
+    bool accounted = true;  // the last batch's copy statistics are in the server's totals
     bool used = false;
+};
+
+// Host threads that copy a submitted block into pinned staging, each a share
+// of the channel rows (one host thread's memcpy is far slower than the
+// host-to-device link).
+class CopyPool {
+  public:
+    explicit CopyPool(int n) {
+        for (int i = 0; i < n; ++i)
+            th_.emplace_back([this]() { run(); });
+    }
+    ~CopyPool() {
+        {
+            std::lock_guard<std::mutex> lk(mu_);
+            stop_ = true;
+        }
+        cv_.notify_all();
+        for (auto &t : th_)
+            t.join();
+    }
+    // rows [0, n) of `bytes` bytes from src (row pitch sp) to dst (pitch dp);
+    // the caller takes one share and waits for the others.
+    void copy_rows(uint8_t *dst, int64_t dp, const uint8_t *src, int64_t sp, int64_t n,
+                   size_t bytes) {
+        const int parts = (int)th_.size() + 1;
+        std::unique_lock<std::mutex> lk(mu_);
+        job_ = Job{dst, dp, src, sp, n, bytes, parts};
+        next_ = 1;
+        left_ = parts - 1;
+        ++gen_;
+        lk.unlock();
+        cv_.notify_all();
+        part(job_, 0);
+        lk.lock();
+        cv_done_.wait(lk, [&]() { return left_ == 0; });
+    }
+
+  private:
+    struct Job {
+        uint8_t *dst = nullptr;
+        int64_t dp = 0;
+        const uint8_t *src = nullptr;
+        int64_t sp = 0, n = 0;
+        size_t bytes = 0;
+        int parts = 1;
+    };
+    static void part(const Job &j, int k) {
+        const int64_t r0 = j.n * k / j.parts, r1 = j.n * (k + 1) / j.parts;
+        for (int64_t r = r0; r < r1; ++r)
+            std::memcpy(j.dst + r * j.dp, j.src + r * j.sp, j.bytes);
+    }
+    void run() {
+        uint64_t seen = 0;
+        std::unique_lock<std::mutex> lk(mu_);
+        for (;;) {
+            cv_.wait(lk, [&]() { return stop_ || (gen_ != seen && next_ < job_.parts); });
+            if (stop_)
+                return;
+            const int k = next_++;
+            if (next_ >= job_.parts)
+                seen = gen_;
+            const Job j = job_;
+            lk.unlock();
+            part(j, k);
+            lk.lock();
+            if (--left_ == 0)
+                cv_done_.notify_all();
+        }
+    }
+    std::vector<std::thread> th_;
+    std::mutex mu_;
+    std::condition_variable cv_, cv_done_;
+    Job job_;
+    int next_ = 0, left_ = 0;
+    uint64_t gen_ = 0;
+    bool stop_ = false;
 };
 
 }  // namespace
@@ -114,8 +195,13 @@ struct dd_server_s {
     std::thread worker, completer;
     bool stop = false;
     int64_t window_us = 0;  // how long a partly filled batch waits for more blocks
+    bool window_set = false;  // set by the caller (else derived from the block durations)
     int64_t submitted = 0, completed = 0, rejected = 0, batches = 0, batched_blocks = 0;
     std::vector<double> lat_ms;
+    CopyPool *pool = nullptr;
+    std::mutex submit_mu;  // one staging copy at a time through the pool
+    int64_t staged_bytes = 0, h2d_bytes = 0, d2h_bytes = 0;  // copy statistics
+    double staged_ms = 0.0, h2d_ms = 0.0, d2h_ms = 0.0;
 };
 
 namespace {
@@ -144,6 +230,9 @@ void free_all(dd_server_s *v) {
         cudaFree(l.d_counter);
         if (l.done)
             cudaEventDestroy(l.done);
+        for (cudaEvent_t &ev : l.t)
+            if (ev)
+                cudaEventDestroy(ev);
         if (l.s)
             cudaStreamDestroy(l.s);
         l = Lane{};
@@ -239,6 +328,8 @@ dd_status start(dd_server_s *v) {
                                  cudaHostAllocDefault) == cudaSuccess;
         ok = ok && cudaMalloc((void **)&l.d_counter, sizeof(int)) == cudaSuccess;
         ok = ok && cudaEventCreateWithFlags(&l.done, cudaEventDisableTiming) == cudaSuccess;
+        for (cudaEvent_t &ev : l.t)
+            ok = ok && cudaEventCreate(&ev) == cudaSuccess;
     }
     if (!ok) {
         cudaGetLastError();
@@ -246,8 +337,35 @@ dd_status start(dd_server_s *v) {
         return fail(DD_ERR_NOMEM, "server device/pinned allocation failed");
     }
     v->device_bytes = tails + (int64_t)slot_bytes * nslots;
+    if (!v->window_set) {
+        // 1/64 of the shortest block duration, at most 100 ms: far inside the
+        // real-time deadline (a block's own duration), long enough for blocks
+        // of other beams arriving meanwhile to share a launch.
+        double shortest = 1e30;
+        for (auto &b : v->beams)
+            shortest = std::min(shortest, (double)b.B * b.plan->tsamp);
+        v->window_us = (int64_t)std::min(100000.0, shortest * 1e6 / 64.0);
+    }
+    const unsigned hc = std::thread::hardware_concurrency();
+    v->pool = new (std::nothrow) CopyPool((int)std::max(1u, std::min(7u, hc > 1 ? hc / 2 : 1u)));
     v->started = true;
     return DD_OK;
+}
+
+// Add the copy statistics of the lane's last (completed) batch to the
+// server's totals, once.  Caller holds v->mu.
+void account_lane(dd_server_s *v, Lane &l) {
+    if (l.accounted)
+        return;
+    float ms_in = 0.0f, ms_out = 0.0f;
+    if (cudaEventElapsedTime(&ms_in, l.t[0], l.t[1]) == cudaSuccess &&
+        cudaEventElapsedTime(&ms_out, l.t[2], l.t[3]) == cudaSuccess) {
+        v->h2d_bytes += l.h2d_bytes;
+        v->d2h_bytes += l.d2h_bytes;
+        v->h2d_ms += ms_in;
+        v->d2h_ms += ms_out;
+    }
+    l.accounted = true;
 }
 
 // Launch one batch of (request, slot) pairs on lane l.  Caller holds no lock.
@@ -256,8 +374,15 @@ dd_status launch_batch(dd_server_s *v, Lane &l, const std::vector<dd_ticket> &ti
     cudaStream_t s = l.s;
     const int elem = v->elem;
     cudaError_t e = cudaSuccess;
-    if (l.used)  // descriptors of the previous batch on this lane must be consumed
+    if (l.used) {  // descriptors of the previous batch on this lane must be consumed
         e = cudaEventSynchronize(l.done);
+        std::lock_guard<std::mutex> lk(v->mu);
+        if (e == cudaSuccess)
+            account_lane(v, l);
+    }
+    l.h2d_bytes = l.d2h_bytes = 0;
+    if (e == cudaSuccess)
+        e = cudaEventRecord(l.t[0], s);
     int64_t tile0 = 0;
     for (size_t i = 0; i < rs.size() && e == cudaSuccess; ++i) {
         SrvReq &r = *rs[i];
@@ -279,6 +404,7 @@ dd_status launch_batch(dd_server_s *v, Lane &l, const std::vector<dd_ticket> &ti
             e = cudaMemcpy2DAsync(in + (size_t)b.S * elem, pitch_b, v->staging[r.staging],
                                   (size_t)b.B * elem, (size_t)b.B * elem, nchan,
                                   cudaMemcpyHostToDevice, s);
+        l.h2d_bytes += (int64_t)b.B * elem * nchan;
         // new tail: the last S samples of [tail | block]
         if (e == cudaSuccess && b.S > 0)
             e = cudaMemcpy2DAsync(b.tail, (size_t)b.tail_pitch * elem, in + (size_t)b.B * elem,
@@ -310,6 +436,8 @@ dd_status launch_batch(dd_server_s *v, Lane &l, const std::vector<dd_ticket> &ti
                             cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess)
         e = cudaMemsetAsync(l.d_counter, 0, sizeof(int), s);
+    if (e == cudaSuccess)
+        e = cudaEventRecord(l.t[1], s);
     if (e != cudaSuccess)
         return fail(DD_ERR_CUDA, std::string("server batch staging: ") + cudaGetErrorString(e));
     dd::KArgs a{};
@@ -336,6 +464,7 @@ dd_status launch_batch(dd_server_s *v, Lane &l, const std::vector<dd_ticket> &ti
     if (e != cudaSuccess)
         return fail(DD_ERR_CUDA, std::string("server kernel launch: ") + cudaGetErrorString(e));
     dd::count_launch(1);
+    e = cudaEventRecord(l.t[2], s);
     // results into the callers' buffers
     for (size_t i = 0; i < rs.size() && e == cudaSuccess; ++i) {
         SrvReq &r = *rs[i];
@@ -347,11 +476,18 @@ dd_status launch_batch(dd_server_s *v, Lane &l, const std::vector<dd_ticket> &ti
         e = cudaMemcpy2DAsync(r.out_host, (size_t)r.out_pitch * sizeof(float), sl.out + col0,
                               (size_t)v->out_pitch * sizeof(float), (size_t)r.nsamp * sizeof(float),
                               b.plan->ndm, cudaMemcpyDeviceToHost, s);
+        l.d2h_bytes += r.nsamp * (int64_t)sizeof(float) * b.plan->ndm;
         if (e == cudaSuccess)
             e = cudaEventRecord(r.done, s);
     }
     if (e == cudaSuccess)
+        e = cudaEventRecord(l.t[3], s);
+    if (e == cudaSuccess)
         e = cudaEventRecord(l.done, s);
+    {
+        std::lock_guard<std::mutex> lk(v->mu);
+        l.accounted = false;
+    }
     l.used = true;
     if (e != cudaSuccess)
         return fail(DD_ERR_CUDA, std::string("server result copy: ") + cudaGetErrorString(e));
@@ -579,12 +715,22 @@ dd_status dd_submit(dd_server_t v, int beam_id, const void *block_host, int64_t 
     // Copy the block into pinned staging (outside the lock: the buffer is ours).
     uint8_t *dst = static_cast<uint8_t *>(v->staging[sidx]);
     const int64_t nchan = b.plan->nchan, B = b.B, elem = v->elem;
+    CopyPool *pool = v->pool;
     lk.unlock();
     const uint8_t *src = static_cast<const uint8_t *>(block_host);
-    for (int64_t c = 0; c < nchan; ++c)
-        std::memcpy(dst + c * B * elem, src + c * in_pitch * elem, (size_t)(B * elem));
+    const auto c0 = Clock::now();
+    if (pool) {
+        std::lock_guard<std::mutex> plk(v->submit_mu);
+        pool->copy_rows(dst, B * elem, src, in_pitch * elem, nchan, (size_t)(B * elem));
+    } else {
+        for (int64_t c = 0; c < nchan; ++c)
+            std::memcpy(dst + c * B * elem, src + c * in_pitch * elem, (size_t)(B * elem));
+    }
+    const double copy_ms = std::chrono::duration<double, std::milli>(Clock::now() - c0).count();
     cudaError_t e = cudaEventCreateWithFlags(&r.done, cudaEventDisableTiming);
     lk.lock();
+    v->staged_bytes += nchan * B * elem;
+    v->staged_ms += copy_ms;
     if (e != cudaSuccess) {
         v->staging_busy[sidx] = false;
         return fail(DD_ERR_CUDA, "event creation failed");
@@ -626,6 +772,7 @@ dd_status dd_server_set_batch_window(dd_server_t v, int64_t microseconds) {
         return fail(DD_ERR_INVALID, "batch window must be 0..10 s");
     std::lock_guard<std::mutex> lk(v->mu);
     v->window_us = microseconds;
+    v->window_set = true;
     return DD_OK;
 }
 
@@ -653,6 +800,17 @@ dd_status dd_server_get_stats(dd_server_t v, dd_server_stats *s) {
     s->mean_batch = v->batches ? (double)v->batched_blocks / (double)v->batches : 0.0;
     s->slots = (int)v->slots.size();
     s->device_bytes = v->device_bytes;
+    if (v->completed == v->submitted)  // nothing in flight: count the lanes' last batches
+        for (auto &l : v->lanes)
+            if (l.used && !l.accounted && cudaEventQuery(l.done) == cudaSuccess)
+                account_lane(v, l);
+    s->staging_bytes = v->staged_bytes;
+    s->staging_ms = v->staged_ms;
+    s->h2d_bytes = v->h2d_bytes;
+    s->h2d_ms = v->h2d_ms;
+    s->d2h_bytes = v->d2h_bytes;
+    s->d2h_ms = v->d2h_ms;
+    s->batch_window_us = v->window_us;
     return DD_OK;
 }
 
@@ -680,6 +838,7 @@ dd_status dd_server_destroy(dd_server_t v) {
         if (kv.second.done)
             cudaEventDestroy(kv.second.done);
     free_all(v);
+    delete v->pool;
     delete v;
     return st;
 }

@@ -264,3 +264,25 @@ def test_channelise_validates_before_touching_a_gpu(dd):
     # fewer than M*T raw samples: no spectra, a no-op that needs no device
     assert dd.lib.dd_channelise(None, 252, 2, 63, 16, 4, None, 1, 0.5, None, 0, None) == 0
 
+
+
+def test_execute_detect_validates_before_touching_a_gpu(dd):
+    """dd_execute_detect takes uint8 input, nlevels 1..9 and aligned outputs;
+    anything else is DD_ERR_INVALID from host checks alone."""
+    import ctypes
+    w = fb.SMALL
+    p = dd.Plan(w.nchan, w.fch1, w.foff, w.tsamp, w.dm_list())
+    S = p.maxshift
+    lib = dd.lib
+    good = dict(inp=4096, dtype=0, pitch=8512, nin=8192 + S, out=8192, opitch=8192,
+                nout=8192, nlev=9, mean=1024, std=2048, snr=4096, tpk=8192)
+    bad = [dict(dtype=1), dict(dtype=2), dict(nlev=0), dict(nlev=10), dict(nin=8192 + S - 1),
+           dict(inp=4097), dict(mean=1028), dict(tpk=0), dict(nout=0), dict(nout=(1 << 21) + 1)]
+    for b in bad:
+        a = {**good, **b}
+        st = lib.dd_execute_detect(p.handle, ctypes.c_void_p(a["inp"]), a["dtype"], a["pitch"],
+                                   a["nin"], ctypes.c_void_p(a["out"]), a["opitch"], a["nout"],
+                                   a["nlev"], ctypes.c_void_p(a["mean"]),
+                                   ctypes.c_void_p(a["std"]), ctypes.c_void_p(a["snr"]),
+                                   ctypes.c_void_p(a["tpk"]), None)
+        assert st == -1, b

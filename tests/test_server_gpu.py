@@ -64,7 +64,8 @@ class Stream:
 
 def _serve(dd, streams, budget=8 << 30, inflight=8, interleave=True, window_us=0):
     srv = dd.Server(budget, inflight, "u8")
-    srv.set_batch_window(window_us)
+    if window_us is not None:
+        srv.set_batch_window(window_us)
     ids = [srv.add_beam(s.plan(dd), s.B) for s in streams]
     pending = {}
     order = [(i, k) for k in range(max(s.nblocks for s in streams)) for i in range(len(streams))
@@ -125,6 +126,24 @@ def test_full_queue_returns_busy_and_all_accepted_blocks_complete(dd, oracle_lib
     stats, busy = _serve(dd, streams, budget=64 << 20, inflight=1, interleave=True)
     assert busy > 0 and stats["rejected_busy"] == busy
     assert stats["slots"] == 1
+    for s in streams:
+        s.check(oracle_lib)
+
+
+def test_default_batch_window_and_copy_statistics(dd, oracle_lib):
+    """Without an explicit window the server waits up to 1/64 of the shortest
+    block duration for more ready blocks; its statistics count every block's
+    staging, host-to-device and device-to-host bytes with positive times, and
+    the results stay bit-exact."""
+    streams = [Stream(oracle_lib, 40 + i, 64, 32, 64.0, 4096, 3) for i in range(3)]
+    stats, _ = _serve(dd, streams, window_us=None)
+    assert stats["batch_window_us"] == int(4096 * 64e-6 * 1e6 / 64)
+    n = stats["completed"]
+    assert n == 9 and stats["staging_bytes"] == n * 64 * 4096
+    assert stats["h2d_bytes"] == stats["staging_bytes"]
+    assert stats["d2h_bytes"] == sum(4 * 32 * (4096 - s.S if k == 0 else 4096)
+                                     for s in streams for k in range(3))
+    assert stats["staging_ms"] > 0 and stats["h2d_ms"] > 0 and stats["d2h_ms"] > 0
     for s in streams:
         s.check(oracle_lib)
 
