@@ -178,6 +178,89 @@ __device__ __forceinline__ void record(int *status, int code) {
     atomicCAS(status, kDevOk, code);
 }
 
+// Tensor-memory (TMEM) access of one warp: N consecutive 32-bit columns of
+// its 32 lanes (thread i: lane i).  The FP16/FP32 consumers keep their
+// running sums and compensations there (written and read once per block of
+// channels).
+template <int N>
+__device__ __forceinline__ void tm_ld(uint32_t taddr, uint32_t (&v)[N]) {
+    static_assert(N == 4 || N == 8 || N == 16, "TMEM load width");
+    if constexpr (N == 4)
+        asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0, %1, %2, %3}, [%4];"
+                     : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3])
+                     : "r"(taddr)
+                     : "memory");
+    else if constexpr (N == 8)
+        asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, "
+                     "[%8];"
+                     : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]),
+                       "=r"(v[6]), "=r"(v[7])
+                     : "r"(taddr)
+                     : "memory");
+    else
+        asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, "
+                     "%8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+                     : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]),
+                       "=r"(v[6]), "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]),
+                       "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+                     : "r"(taddr)
+                     : "memory");
+}
+
+template <int N>
+__device__ __forceinline__ void tm_st(uint32_t taddr, const uint32_t (&v)[N]) {
+    static_assert(N == 4 || N == 8 || N == 16, "TMEM store width");
+    if constexpr (N == 4)
+        asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1, %2, %3, %4};" ::"r"(taddr),
+                     "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3])
+                     : "memory");
+    else if constexpr (N == 8)
+        asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, "
+                     "%8};" ::"r"(taddr),
+                     "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]),
+                     "r"(v[7])
+                     : "memory");
+    else
+        asm volatile("tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, "
+                     "%8, %9, %10, %11, %12, %13, %14, %15, %16};" ::"r"(taddr),
+                     "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]),
+                     "r"(v[7]), "r"(v[8]), "r"(v[9]), "r"(v[10]), "r"(v[11]), "r"(v[12]),
+                     "r"(v[13]), "r"(v[14]), "r"(v[15])
+                     : "memory");
+}
+
+__device__ __forceinline__ void tm_wait_ld() {
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tm_wait_st() {
+    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+}
+
+// Registers written by tcgen05.ld hold their values only after
+// tcgen05.wait::ld, which the compiler does not know: after each wait the
+// loaded registers pass through an empty volatile asm that redefines them, so
+// no use of them can be scheduled above the wait.
+template <int N>
+__device__ __forceinline__ void reg_fence(uint32_t (&v)[N]) {
+#pragma unroll
+    for (int i = 0; i < N; ++i)
+        asm volatile("" : "+r"(v[i]));
+}
+
+// TMEM columns the FP16/FP32 consumers of a <DT, NW> kernel allocate: per
+// warp the running sums S (DT * NW * samples per word) and compensations C
+// (DT * NW: one FP32 word, or for FP16 one packed bf16 pair, per output
+// word), for up to ceil(max_consumer_warps / 4) warps per lane quarter,
+// rounded up to a power of two (at least 32).
+DD_HD constexpr int tm_sum_cols(int elem, int dt, int nw) { return dt * nw * (4 / elem) + dt * nw; }
+DD_HD constexpr int tm_alloc_cols(int elem, int dt, int nw) {
+    const int need = ((max_consumer_warps(dt, nw) + 3) / 4) * tm_sum_cols(elem, dt, nw);
+    int c = 32;
+    while (c < need)
+        c *= 2;
+    return c;
+}
+
 // Store (first widening of a uint8 SWAR block) or add (later blocks) four
 // exact integer sums to out[t..t+3].  Later blocks use fire-and-forget
 // vector reductions: the values are integers below 2^24, so FP32 addition is
@@ -355,9 +438,27 @@ __global__ void __launch_bounds__(32 * (max_consumer_warps(DT, NW) + 1 + (ELEM <
             mbar_init(empty0 + 8 * b, ncw);
             mbar_init(raw0 + 8 * b, 1);
         }
-        if (DET)
+        if (DET || ELEM > 1)
             mbar_init(ep_bar, ncw);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    // FP16/FP32: consumer warp 0 allocates the TMEM of the running sums (the
+    // address goes to the epilogue slot of shared memory) and frees it at the
+    // end.  If another CTA on the SM holds too many columns the allocation
+    // waits until it finishes.
+    constexpr int TM_COLS = tm_alloc_cols(ELEM, DT, NW);
+    uint32_t *tm_slot = reinterpret_cast<uint32_t *>(ep_flags);
+    if constexpr (ELEM > 1) {
+        static_assert(TM_COLS <= 512, "TMEM columns of the running sums");
+        if (warp == 0) {
+            asm volatile(
+                "tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                    smem_addr(tm_slot)),
+                "n"(TM_COLS)
+                : "memory");
+            asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        }
     }
     __syncthreads();
 
@@ -608,27 +709,33 @@ __global__ void __launch_bounds__(32 * (max_consumer_warps(DT, NW) + 1 + (ELEM <
     const int thr_off = ELEM * (wti * SPAN) + 4 * lane;
     const uint32_t one = a.one;
 
-    uint32_t L1[DT][NW], L2[DT][NW];                            // uint8 SWAR
-    float P[DT][NW][SPW], S[DT][NW][SPW], C[DT][NW][SPW];      // floats
-    // FP16 input keeps the compensation terms of a word's two samples as one
-    // packed bf16 pair.  A compensation is a sum of FP32 rounding errors, at
-    // most about 64 * 2^-24 |S|, so its 8 significant bits move the result by
-    // less than 2^-27 |S|; the pair frees a register per output word.
-    __nv_bfloat162 C2[DT][NW];
+    uint32_t L1[DT][NW], L2[DT][NW];  // uint8 SWAR
+    float P[DT][NW][SPW];             // FP16/FP32 block partials
 #pragma unroll
     for (int j = 0; j < DT; ++j)
 #pragma unroll
         for (int k = 0; k < NW; ++k) {
             L1[j][k] = 0u;
             L2[j][k] = 0u;
-            C2[j][k] = __float2bfloat162_rn(0.f);
 #pragma unroll
-            for (int e = 0; e < SPW; ++e) {
+            for (int e = 0; e < SPW; ++e)
                 P[j][k][e] = 0.f;
-                S[j][k][e] = 0.f;
-                C[j][k][e] = 0.f;
-            }
         }
+    // FP16/FP32: the running sums S and compensations C of this thread's
+    // outputs live in its TMEM lane (warp w: lane quarter w % 4, columns
+    // (w / 4) * tm_sum_cols ..): S of DM j, word k, sample e at column
+    // (j*NW + k)*SPW + e, C of DM j, word k at DT*NW*SPW + j*NW + k.  FP16
+    // keeps the compensations of a word's two samples as one packed bf16
+    // pair: a compensation is a sum of FP32 rounding errors, at most about
+    // 64 * 2^-24 |S|, so its 8 significant bits move the result by less than
+    // 2^-27 |S|.
+    uint32_t tm = 0;
+    if constexpr (ELEM > 1) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        tm = *tm_slot + ((uint32_t)(32 * (warp & 3)) << 16) +
+             (uint32_t)((warp >> 2) * tm_sum_cols(ELEM, DT, NW));
+    }
+    bool fresh = true;  // no block of the current tile closed yet
 
     // Current tile (from the stage records).
     int beam = 0, kthr = 0;
@@ -666,68 +773,99 @@ __global__ void __launch_bounds__(32 * (max_consumer_warps(DT, NW) + 1 + (ELEM <
         flushed_once = true;
     };
 
+    constexpr int NS = ELEM > 1 ? NW * SPW : 4;          // S columns per DM (floats)
+    constexpr int CC0 = DT * NW * SPW;                   // first C column
+    // Close a block of channels: (S, C) += P by TwoSum, one DM at a time
+    // (the first block of a tile sets S = P, C = 0); P is cleared.
     auto block_float = [&]() {
 #pragma unroll
-        for (int j = 0; j < DT; ++j)
+        for (int j = 0; j < DT; ++j) {
+            uint32_t sv[NS], cv[NW];
+            if (fresh) {
 #pragma unroll
-            for (int k = 0; k < NW; ++k) {
-                float errs[SPW];
-#pragma unroll
-                for (int e = 0; e < SPW; ++e) {
-                    // TwoSum(S, P): S + P = s + err exactly.
-                    const float p = P[j][k][e];
-                    const float s = __fadd_rn(S[j][k][e], p);
-                    const float bp = __fsub_rn(s, S[j][k][e]);
-                    errs[e] = __fadd_rn(__fsub_rn(S[j][k][e], __fsub_rn(s, bp)),
-                                        __fsub_rn(p, bp));
-                    S[j][k][e] = s;
-                    P[j][k][e] = 0.f;
-                }
-                if constexpr (ELEM == 2) {
-                    C2[j][k] = __hadd2(C2[j][k], __floats2bfloat162_rn(errs[0], errs[SPW - 1]));
-                } else {
+                for (int k = 0; k < NW; ++k) {
+                    cv[k] = 0u;
 #pragma unroll
                     for (int e = 0; e < SPW; ++e)
-                        C[j][k][e] = __fadd_rn(C[j][k][e], errs[e]);
+                        sv[k * SPW + e] = __float_as_uint(P[j][k][e]);
+                }
+            } else {
+                tm_ld<NS>(tm + (uint32_t)(j * NS), sv);
+                tm_ld<NW>(tm + (uint32_t)(CC0 + j * NW), cv);
+                tm_wait_ld();
+                reg_fence(sv);
+                reg_fence(cv);
+#pragma unroll
+                for (int k = 0; k < NW; ++k) {
+                    float errs[SPW];
+#pragma unroll
+                    for (int e = 0; e < SPW; ++e) {
+                        // TwoSum(S, P): S + P = s + err exactly.
+                        const float S0 = __uint_as_float(sv[k * SPW + e]);
+                        const float p = P[j][k][e];
+                        const float sum = __fadd_rn(S0, p);
+                        const float bp = __fsub_rn(sum, S0);
+                        errs[e] = __fadd_rn(__fsub_rn(S0, __fsub_rn(sum, bp)), __fsub_rn(p, bp));
+                        sv[k * SPW + e] = __float_as_uint(sum);
+                    }
+                    if constexpr (ELEM == 2) {
+                        __nv_bfloat162 c2 = *reinterpret_cast<__nv_bfloat162 *>(&cv[k]);
+                        c2 = __hadd2(c2, __floats2bfloat162_rn(errs[0], errs[SPW - 1]));
+                        cv[k] = *reinterpret_cast<uint32_t *>(&c2);
+                    } else {
+                        cv[k] = __float_as_uint(__fadd_rn(__uint_as_float(cv[k]), errs[0]));
+                    }
                 }
             }
-    };
-    // Compensation of output (j, k, e) as FP32.
-    auto comp = [&](int j, int k, int e) -> float {
-        if constexpr (ELEM == 2)
-            return e == 0 ? __low2float(C2[j][k]) : __high2float(C2[j][k]);
-        else
-            return C[j][k][e];
+#pragma unroll
+            for (int k = 0; k < NW; ++k)
+#pragma unroll
+                for (int e = 0; e < SPW; ++e)
+                    P[j][k][e] = 0.f;
+            tm_st<NS>(tm + (uint32_t)(j * NS), sv);
+            tm_st<NW>(tm + (uint32_t)(CC0 + j * NW), cv);
+        }
+        tm_wait_st();
+        fresh = false;
     };
 
+    // The tile's outputs S + C, after its last block.
     auto store_float = [&]() {
         const BeamArgs &B = beam_at(a, beam);
 #pragma unroll
         for (int j = 0; j < DT; ++j) {
+            uint32_t sv[NS], cv[NW];
+            tm_ld<NS>(tm + (uint32_t)(j * NS), sv);
+            tm_ld<NW>(tm + (uint32_t)(CC0 + j * NW), cv);
+            tm_wait_ld();
+            reg_fence(sv);
+            reg_fence(cv);
             const int row = B.perm[kthr + j];
+            if (row < 0)
+                continue;
             float *orow = B.out + (int64_t)row * B.out_pitch;
 #pragma unroll
             for (int k = 0; k < NW; ++k) {
                 const int64_t t = tw + SPW * (lane + 32 * k);
-                if (row >= 0) {
-                    if (SPW == 1) {
-                        if (t < B.nsamp_out)
-                            orow[t] = __fadd_rn(S[j][k][0], comp(j, k, 0));
-                    } else {
-                        if (t + 1 < B.nsamp_out) {
-                            *reinterpret_cast<float2 *>(orow + t) =
-                                make_float2(__fadd_rn(S[j][k][0], comp(j, k, 0)),
-                                            __fadd_rn(S[j][k][SPW - 1], comp(j, k, SPW - 1)));
-                        } else if (t < B.nsamp_out) {
-                            orow[t] = __fadd_rn(S[j][k][0], comp(j, k, 0));
-                        }
-                    }
-                }
-                C2[j][k] = __float2bfloat162_rn(0.f);
+                float o[SPW];
 #pragma unroll
                 for (int e = 0; e < SPW; ++e) {
-                    S[j][k][e] = 0.f;
-                    C[j][k][e] = 0.f;
+                    float comp;
+                    if constexpr (ELEM == 2) {
+                        const __nv_bfloat162 c2 = *reinterpret_cast<const __nv_bfloat162 *>(&cv[k]);
+                        comp = e == 0 ? __low2float(c2) : __high2float(c2);
+                    } else {
+                        comp = __uint_as_float(cv[k]);
+                    }
+                    o[e] = __fadd_rn(__uint_as_float(sv[k * SPW + e]), comp);
+                }
+                if (SPW == 1) {
+                    if (t < B.nsamp_out)
+                        orow[t] = o[0];
+                } else if (t + 1 < B.nsamp_out) {
+                    *reinterpret_cast<float2 *>(orow + t) = make_float2(o[0], o[SPW - 1]);
+                } else if (t < B.nsamp_out) {
+                    orow[t] = o[0];
                 }
             }
         }
@@ -821,7 +959,7 @@ __global__ void __launch_bounds__(32 * (max_consumer_warps(DT, NW) + 1 + (ELEM <
         const int b = (int)(g % nst);
         if (!prefetched && !mbar_wait(full0 + 8 * b, (uint32_t)((g / nst) & 1))) {
             record(a.status, kDevTimeout);
-            return;
+            goto consumers_done;
         }
         const StageMeta m = meta[b];
         if (m.beam < 0)
@@ -833,6 +971,7 @@ __global__ void __launch_bounds__(32 * (max_consumer_warps(DT, NW) + 1 + (ELEM <
             tw = m.t0 + (int64_t)wti * SPAN;
             tile_td = m.td;
             tile_t0 = m.t0;
+            fresh = true;
             since_flush = 0;
             flushed_once = false;
         }
@@ -876,7 +1015,7 @@ __global__ void __launch_bounds__(32 * (max_consumer_warps(DT, NW) + 1 + (ELEM <
                     if (left == 2 &&
                         !mbar_wait(full0 + 8 * bn, (uint32_t)(((g + 1) / nst) & 1))) {
                         record(a.status, kDevTimeout);
-                        return;
+                        goto consumers_done;
                     }
                     onn = ahead(tbn, (2 - left) / DT, (2 - left) % DT);
                 }
@@ -908,8 +1047,28 @@ __global__ void __launch_bounds__(32 * (max_consumer_warps(DT, NW) + 1 + (ELEM <
             if constexpr (DET) {
                 if (!detect_epilogue(a, tile_td, tile_t0, dm_cta, t_cta, ncw, warp, lane, tid,
                                      ep_bar, ep_flags))
-                    return;
+                    goto consumers_done;
             }
+        }
+    }
+consumers_done:
+    if constexpr (ELEM > 1) {
+        // Free the TMEM once every consumer warp is done with it.  The wait is
+        // bounded: a warp that gave up on a timeout arrives here too, and if
+        // one never does the others still free the columns after the limit.
+        tm_wait_st();
+        tm_wait_ld();
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncwarp();
+        if (lane == 0)
+            mbar_arrive(ep_bar);
+        if (!mbar_wait(ep_bar, 0))
+            record(a.status, kDevTimeout);
+        if (warp == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(*tm_slot),
+                         "n"(TM_COLS)
+                         : "memory");
         }
     }
 }
