@@ -56,7 +56,17 @@ TUNE_NSAMP = 65536
 # other run reports traffic null.
 TRAFFIC_SOURCE = ("ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum "
                   "--clock-control none, one step's de-dispersion launches")
-PROFILED_TRAFFIC: list[dict] = []
+PROFILED_TRAFFIC: list[dict] = [
+    # one step, 4096-channel beam, tiles (4,12,1,8,8): a single launch of 42 x 256 tiles
+    {"workload": "lowfreq-4096ch-2000dm-262144", "dtype": "u8", "tiles": [4, 12, 1, 8, 8],
+     "code_sha256": "6ae1b699f549fa784cb461a9ba0907d67d0937b4514e4e5c85b74bc0d33d52cc",
+     "bytes": 5098426624 + 3272573440, "compulsory": 1203281920 + 2097152000},
+    # one step, L-band beam, tiles (4,12,1,8,8): main launch (1008 DMs) + remainder (16 DMs)
+    {"workload": "lband-1024ch-1024dm-131072", "dtype": "u8", "tiles": [4, 12, 1, 8, 8],
+     "code_sha256": "6ae1b699f549fa784cb461a9ba0907d67d0937b4514e4e5c85b74bc0d33d52cc",
+     "bytes": (152664320 + 510945792) + (135869440 + 338432),
+     "compulsory": 151171072 + 536870912},
+]
 
 
 def _sha256(*parts) -> str:
@@ -753,6 +763,7 @@ def roofline_of(adds: float, kernel_ms: float, peak: dict, nominal: float, w: fb
     achieved = adds / (kernel_ms / 1e3)
     prof = profiled_traffic(w.name, dtype, tiles) if traffic_ok else None
     return {"bound": "alu", "achieved": achieved / 1e12, "peak": peak["adds_per_s"] / 1e12,
+            "traffic_over_compulsory": prof["bytes"] / prof["compulsory"] if prof else None,
             "unit": "Tadd/s", "frac": achieved / peak["adds_per_s"],
             "peak_source": f"measured: dd_add_peak microbenchmark ({peak['best']}), "
                            "best of 3 launches",
@@ -1010,8 +1021,15 @@ def main():
                     help="run the Fig. 4 sweeps instead (one JSON line)")
     ap.add_argument("--tiles", default="",
                     help="fixed tile shape dthr,dm_warps,time_warps,cstage[,words]")
+    ap.add_argument("--nsamp-out", type=int, default=0,
+                    help="a shorter output (samples) of the same beam: the smaller case ncu "
+                         "captures run on (0: the workload's own)")
     args = ap.parse_args()
     w = WORKLOADS[args.workload]
+    if args.nsamp_out > 0 and args.nsamp_out != w.nsamp_out:
+        import dataclasses
+        w = dataclasses.replace(w, nsamp_out=args.nsamp_out,
+                                name=f"{w.name}-first{args.nsamp_out}")
     if args.sweep:
         run_sweep(args)
     elif args.impl == "reference":

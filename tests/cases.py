@@ -40,3 +40,18 @@ def sample_cells(rng, ndm: int, nsamp_out: int, n: int):
                 d.append(dd)
                 t.append(tt)
     return np.array(d, dtype=np.int32), np.array(t, dtype=np.int64)
+
+
+_CACHE: dict = {}
+
+
+def lband_input_and_plane(oracle_lib):
+    """The full-size L-band beam (table, dms, S, data) and the oracle's whole
+    plane of it (OpenMP build), computed once per test session."""
+    if "lband" not in _CACHE:
+        w = fb.LBAND
+        table, dms, S, data = workload_input(w)
+        plane = oracle_lib.dedisperse(np.ascontiguousarray(data[:, :w.nsamp_out + S]), table,
+                                      dms, w.nsamp_out, threads=True)
+        _CACHE["lband"] = (table, dms, S, data, plane)
+    return _CACHE["lband"]

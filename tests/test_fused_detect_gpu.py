@@ -13,7 +13,7 @@ import numpy as np
 import pytest
 
 import filterbank as fb
-from tests.cases import workload_input
+from tests.cases import lband_input_and_plane, workload_input
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -86,11 +86,9 @@ def test_fused_search_on_the_full_lband_beam(dd, oracle_lib):
     """The 1024-channel L-band beam at full size (1024 DMs x 131072 samples,
     128 tiles per row): the plane and every search result equal the oracle's."""
     w = fb.LBAND
-    table, dms, S, data = workload_input(w)
+    table, dms, S, data, want_plane = lband_input_and_plane(oracle_lib)
     plan = dd.Plan(w.nchan, w.fch1, w.foff, w.tsamp, dms)
     plane, res = _fused(dd, plan, data, w.nsamp_out + S, w.nsamp_out, 9)
-    want_plane = oracle_lib.dedisperse(np.ascontiguousarray(data[:, :w.nsamp_out + S]), table,
-                                       dms, w.nsamp_out, threads=True)
     _check(oracle_lib, plane, want_plane, res, 9)
 
 
