@@ -325,7 +325,7 @@ static std::vector<dd_tiles> tune_candidates(dd_dtype t) {
     std::vector<dd_tiles> out;
     const int dthrs[3] = {1, 2, 4};
     const int nws[2] = {8, 4};
-    const int dws[8] = {4, 6, 8, 10, 12, 16, 20, 24};
+    const int dws[9] = {4, 6, 8, 10, 12, 13, 16, 20, 24};
     const int wts[3] = {1, 2, 4};
     const int css[5] = {4, 8, 12, 16, 24};
     for (int nw : nws)

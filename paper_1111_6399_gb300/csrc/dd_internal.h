@@ -56,7 +56,7 @@ constexpr int kRowInfoBytes = 256;
 #define DD_HD
 #endif
 DD_HD constexpr int max_consumer_warps(int dm_per_thread, int words) {
-    return words >= 8 ? (dm_per_thread >= 4 ? 12 : dm_per_thread == 2 ? 16 : 20)
+    return words >= 8 ? (dm_per_thread >= 4 ? 13 : dm_per_thread == 2 ? 16 : 20)
                       : (dm_per_thread >= 4 ? 20 : 24);
 }
 

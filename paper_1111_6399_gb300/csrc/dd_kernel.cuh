@@ -465,6 +465,10 @@ __global__ void __launch_bounds__(32 * (max_consumer_warps(DT, NW) + 1 + (ELEM <
     if (warp == ncw) {
         // ------------------------------ producer ------------------------------
         int64_t g = 0;  // ring position of the next stage
+        // g % nst and (g / nst) & 1, advanced with g (no division in the
+        // stage loop)
+        int gb = 0;
+        uint32_t gpar = 0u;
         bool ok = true;
         bool first = true;
         for (;;) {
@@ -502,15 +506,19 @@ __global__ void __launch_bounds__(32 * (max_consumer_warps(DT, NW) + 1 + (ELEM <
                 ds_next[h] = (lane + 32 * h < cstage && c < B.nchan) ? B.dmshift[c] : 0.0f;
             }
             for (int st = 0; st < nstage; ++st, ++g) {
-                const int b = (int)(g % nst);
-                const int64_t n = g / nst;
+                const int b = gb;
+                const uint32_t par = gpar;
+                if (++gb == nst) {
+                    gb = 0;
+                    gpar ^= 1u;
+                }
                 const float ds_cur[2] = {ds_next[0], ds_next[1]};
                 for (int h = 0; h < 2; ++h) {
                     const int c = (st + 1) * cstage + lane + 32 * h;
                     ds_next[h] = (st + 1 < nstage && lane + 32 * h < cstage && c < B.nchan)
                                      ? B.dmshift[c] : 0.0f;
                 }
-                if (n > 0 && !mbar_wait(empty0 + 8 * b, (uint32_t)((n - 1) & 1))) {
+                if (g >= nst && !mbar_wait(empty0 + 8 * b, par ^ 1u)) {
                     ok = false;
                     break;
                 }
@@ -643,9 +651,10 @@ __global__ void __launch_bounds__(32 * (max_consumer_warps(DT, NW) + 1 + (ELEM <
         // chunk j = j0 + l.  Bytes past the copied window only reach samples
         // outside the tile or past nsamp_out.
         const int bw = warp - ncw - 1;
-        for (int64_t g = 0;; ++g) {
-            const int b = (int)(g % nst);
-            if (!mbar_wait(raw0 + 8 * b, (uint32_t)((g / nst) & 1))) {
+        int b = 0;           // g % nst
+        uint32_t par = 0u;   // (g / nst) & 1
+        for (;; b = (b + 1 == nst) ? 0 : b + 1, par ^= (b == 0) ? 1u : 0u) {
+            if (!mbar_wait(raw0 + 8 * b, par)) {
                 record(a.status, kDevTimeout);
                 return;
             }
@@ -955,9 +964,10 @@ __global__ void __launch_bounds__(32 * (max_consumer_warps(DT, NW) + 1 + (ELEM <
     const int q_plain = npairs - (DT == 1 ? 2 : 1);
     bool prefetched = false;
     int2 on = make_int2(0, 0);  // offsets of the next iteration
-    for (int64_t g = 0;; ++g) {
-        const int b = (int)(g % nst);
-        if (!prefetched && !mbar_wait(full0 + 8 * b, (uint32_t)((g / nst) & 1))) {
+    int b = 0;          // g % nst for ring position g
+    uint32_t par = 0u;  // (g / nst) & 1
+    for (;; par ^= (b + 1 == nst) ? 1u : 0u, b = (b + 1 == nst) ? 0 : b + 1) {
+        if (!prefetched && !mbar_wait(full0 + 8 * b, par)) {
             record(a.status, kDevTimeout);
             goto consumers_done;
         }
@@ -991,7 +1001,8 @@ __global__ void __launch_bounds__(32 * (max_consumer_warps(DT, NW) + 1 + (ELEM <
         // if the next one would overflow it.
         const bool widen = !last && since_flush + cstage > FLUSH;
         const bool cross = !last && !widen;
-        const int bn = (int)((g + 1) % nst);
+        const int bn = (b + 1 == nst) ? 0 : b + 1;       // (g + 1) % nst
+        const uint32_t parn = bn == 0 ? par ^ 1u : par;  // ((g + 1) / nst) & 1
         const int *tbn = atab + bn * tab_stride + 2 * kw;
         // Unrolled by two pairs: measured 2 % faster than the plain loop on
         // the L-band beam at (4,12,1,8,8); unrolling by 4 measured slower.
@@ -1013,7 +1024,7 @@ __global__ void __launch_bounds__(32 * (max_consumer_warps(DT, NW) + 1 + (ELEM <
                     onn = ahead(tb, q + (j + 2) / DT, (j + 2) % DT);
                 } else if (cross) {
                     if (left == 2 &&
-                        !mbar_wait(full0 + 8 * bn, (uint32_t)(((g + 1) / nst) & 1))) {
+                        !mbar_wait(full0 + 8 * bn, parn)) {
                         record(a.status, kDevTimeout);
                         goto consumers_done;
                     }

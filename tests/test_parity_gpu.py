@@ -84,7 +84,7 @@ def test_small_workload_bit_exact(dd, oracle_lib):
 
 TILES_U8 = [(4, 12, 1, 8), (4, 4, 2, 8), (2, 3, 1, 4), (1, 1, 1, 16), (4, 5, 2, 4),
             (4, 10, 2, 8, 4), (2, 12, 2, 8, 4), (1, 24, 1, 4, 4), (2, 8, 1, 32, 4),
-            (1, 12, 1, 48, 4), (4, 6, 1, 4), (2, 16, 1, 8), (1, 16, 1, 4)]
+            (1, 12, 1, 48, 4), (4, 6, 1, 4), (2, 16, 1, 8), (1, 16, 1, 4), (4, 13, 1, 8)]
 
 
 def _case_that_fits(dd, rng, nchan, ndm, nsamp_out, kind, tiles, dm_hi=80.0):
@@ -169,6 +169,22 @@ def test_float_fuzz(dd, oracle_lib, kind, seed):
         _check_float(got, want, asum)
     else:
         assert np.array_equal(got.astype(np.float64), want)
+
+
+@pytest.mark.parametrize("kind", ["f32-frac", "f16-frac"])
+@pytest.mark.parametrize("tiles", [(4, 13, 1, 8), (4, 12, 1, 8), (2, 16, 1, 8)])
+def test_float_fuzz_wide_tiles(dd, oracle_lib, kind, tiles):
+    """The widest CTAs of 4 and 2 DMs per thread (16 warps with the producer
+    and the phase builders): ragged sizes, every cell within the bound."""
+    rng = np.random.default_rng(500 + sum(tiles) + len(kind))
+    nchan = int(rng.integers(3, 300))
+    ndm = int(rng.integers(60, 150))
+    nsamp_out = int(rng.integers(1, 5000))
+    plan, table, dms, nin, data = _case_that_fits(dd, rng, nchan, ndm, nsamp_out, kind, tiles)
+    got = _run(dd, plan, data, nin, nsamp_out)
+    want, asum = oracle_lib.dedisperse(np.ascontiguousarray(data[:, :nin]), table, dms,
+                                       nsamp_out, with_abssum=True)
+    _check_float(got, want, asum)
 
 
 def test_extreme_values_u8_4096_channels(dd, oracle_lib):
