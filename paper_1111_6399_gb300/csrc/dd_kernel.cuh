@@ -389,7 +389,7 @@ __device__ __noinline__ bool detect_epilogue(const KArgs &a, int td, int64_t t0,
 // ---------------------------------------------------------------------------
 // DET: the uint8 form that also searches the finished plane for pulses
 // (fused detection, see detect_epilogue below).
-template <int ELEM, int DT, int NW, bool DET = false>
+template <int ELEM, int DT, int NW, bool DET = false, int CS = 0>
 __global__ void __launch_bounds__(32 * (max_consumer_warps(DT, NW) + 1 + (ELEM < 4 ? kMaxBuilders : 0)), 1)
     dedisperse_kernel(const __grid_constant__ KArgs a) {
     constexpr int NPH = 4 / ELEM;            // phase copies per row
@@ -406,7 +406,7 @@ __global__ void __launch_bounds__(32 * (max_consumer_warps(DT, NW) + 1 + (ELEM <
     const int dm_cta = DT * a.dm_warps;
     const int t_cta = SPAN * a.time_warps;
 
-    const int cstage = a.cstage;
+    const int cstage = CS > 0 ? CS : a.cstage;  // CS: channels per stage fixed at compile time
     const int nst = a.nstages;
     const int stage_bytes = a.stage_bytes;
     const int tab_stride = cstage * dm_cta;  // ints per stage in the offset table
@@ -1004,9 +1004,12 @@ __global__ void __launch_bounds__(32 * (max_consumer_warps(DT, NW) + 1 + (ELEM <
         const int bn = (b + 1 == nst) ? 0 : b + 1;       // (g + 1) % nst
         const uint32_t parn = bn == 0 ? par ^ 1u : par;  // ((g + 1) / nst) & 1
         const int *tbn = atab + bn * tab_stride + 2 * kw;
-        // Unrolled by two pairs: measured 2 % faster than the plain loop on
-        // the L-band beam at (4,12,1,8,8); unrolling by 4 measured slower.
-#pragma unroll 2
+        // Unrolled by two pairs (measured 2 % faster than the plain loop on
+        // the L-band beam at (4,12,1,8,8); unrolling by 4 measured slower),
+        // or whole for uint8 with the stage size fixed at compile time
+        // (measured 3 % faster than by two on the 4096-channel beam; FP16
+        // measured 3 % slower whole).
+#pragma unroll((CS > 0 && ELEM == 1) ? CS : 2)
         for (int q = 0; q < q_plain; ++q) {
 #pragma unroll
             for (int j = 0; j < DT; ++j) {
@@ -1015,6 +1018,7 @@ __global__ void __launch_bounds__(32 * (max_consumer_warps(DT, NW) + 1 + (ELEM <
                 on = onn;
             }
         }
+#pragma unroll(CS > 0 ? CS : 1)
         for (int q = q_plain; q < npairs; ++q) {
 #pragma unroll
             for (int j = 0; j < DT; ++j) {
@@ -1084,9 +1088,9 @@ consumers_done:
     }
 }
 
-template <int ELEM, int DT, int NW, bool DET = false>
+template <int ELEM, int DT, int NW, bool DET = false, int CS = 0>
 cudaError_t launch_one(const KArgs &a, unsigned grid, int threads, int smem, cudaStream_t s) {
-    auto k = dedisperse_kernel<ELEM, DT, NW, DET>;
+    auto k = dedisperse_kernel<ELEM, DT, NW, DET, CS>;
     // Raise the dynamic shared-memory limit only when a launch needs more than
     // before (so a launch inside a stream capture never changes attributes
     // after an eager launch of the same shape).
@@ -1115,6 +1119,12 @@ cudaError_t launch_elem(const KArgs &a, unsigned grid, int threads, int smem, cu
             return launch_one<1, 4, 8, true>(a, grid, threads, smem, s);
         }
     }
+    // The tuned shape of each element size at 4 DMs x 8 words also has an
+    // instantiation with its stage size fixed, which unrolls the stage loop
+    // and resolves its hand-over branches at compile time.
+    constexpr int kFixedStage = ELEM == 1 ? 8 : ELEM == 2 ? 12 : 24;
+    if (nw == 8 && dthr == 4 && a.cstage == kFixedStage)
+        return launch_one<ELEM, 4, 8, false, kFixedStage>(a, grid, threads, smem, s);
     if (nw == 4) {
         switch (dthr) {
         case 1: return launch_one<ELEM, 1, 4>(a, grid, threads, smem, s);

@@ -172,10 +172,13 @@ def test_float_fuzz(dd, oracle_lib, kind, seed):
 
 
 @pytest.mark.parametrize("kind", ["f32-frac", "f16-frac"])
-@pytest.mark.parametrize("tiles", [(4, 13, 1, 8), (4, 12, 1, 8), (2, 16, 1, 8)])
+@pytest.mark.parametrize("tiles", [(4, 13, 1, 8), (4, 12, 1, 8), (2, 16, 1, 8),
+                                   (4, 12, 1, 12), (4, 10, 1, 24)])
 def test_float_fuzz_wide_tiles(dd, oracle_lib, kind, tiles):
     """The widest CTAs of 4 and 2 DMs per thread (16 warps with the producer
-    and the phase builders): ragged sizes, every cell within the bound."""
+    and the phase builders), and the stage sizes with a compile-time
+    instantiation (12 channels for FP16, 24 for FP32): ragged sizes, every
+    cell within the bound."""
     rng = np.random.default_rng(500 + sum(tiles) + len(kind))
     nchan = int(rng.integers(3, 300))
     ndm = int(rng.integers(60, 150))
