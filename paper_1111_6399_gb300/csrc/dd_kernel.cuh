@@ -1116,6 +1116,8 @@ cudaError_t launch_elem(const KArgs &a, unsigned grid, int threads, int smem, cu
         if (a.det_s1) {  // fused detection: uint8, 4 DMs x 8 words per thread
             if (nw != 8 || dthr != 4)
                 return cudaErrorInvalidValue;
+            if (a.cstage == 8)
+                return launch_one<1, 4, 8, true, 8>(a, grid, threads, smem, s);
             return launch_one<1, 4, 8, true>(a, grid, threads, smem, s);
         }
     }
