@@ -59,12 +59,16 @@ TRAFFIC_SOURCE = ("ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum "
 PROFILED_TRAFFIC: list[dict] = [
     # one step, 4096-channel beam, tiles (4,12,1,8,8): a single launch of 42 x 256 tiles
     {"workload": "lowfreq-4096ch-2000dm-262144", "dtype": "u8", "tiles": [4, 12, 1, 8, 8],
-     "code_sha256": "6ae1b699f549fa784cb461a9ba0907d67d0937b4514e4e5c85b74bc0d33d52cc",
-     "bytes": 5098426624 + 3272573440, "compulsory": 1203281920 + 2097152000},
+     "code_sha256": "81b799d99197287efbc40fdfa738662c596bf5a398684d03d44737ff4d1d8816",
+     "bytes": 4790403072 + 2875413504, "compulsory": 1203281920 + 2097152000},
+    # one step, the same beam stored as FP16, tiles (4,12,1,12,8): a single launch
+    {"workload": "lowfreq-4096ch-2000dm-262144", "dtype": "f16", "tiles": [4, 12, 1, 12, 8],
+     "code_sha256": "81b799d99197287efbc40fdfa738662c596bf5a398684d03d44737ff4d1d8816",
+     "bytes": 20705216768 + 2230952960, "compulsory": 2406563840 + 2097152000},
     # one step, L-band beam, tiles (4,12,1,8,8): main launch (1008 DMs) + remainder (16 DMs)
     {"workload": "lband-1024ch-1024dm-131072", "dtype": "u8", "tiles": [4, 12, 1, 8, 8],
-     "code_sha256": "6ae1b699f549fa784cb461a9ba0907d67d0937b4514e4e5c85b74bc0d33d52cc",
-     "bytes": (152664320 + 510945792) + (135869440 + 338432),
+     "code_sha256": "81b799d99197287efbc40fdfa738662c596bf5a398684d03d44737ff4d1d8816",
+     "bytes": (153392640 + 506828544) + (135646464 + 358912),
      "compulsory": 151171072 + 536870912},
 ]
 
