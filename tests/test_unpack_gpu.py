@@ -30,7 +30,8 @@ def _run(dd, raw, nbits, nchan, nsamp, offset=0, pitch_extra=16):
 
 @pytest.mark.parametrize("nbits", [1, 2, 4, 8])
 @pytest.mark.parametrize("nchan,nsamp", [(128, 1000), (256, 129), (1024, 4096), (136, 333),
-                                         (8, 5), (24, 130), (384, 1)])
+                                         (8, 5), (24, 130), (384, 1), (512, 3 * 256 + 17),
+                                         (128, 256), (256, 16 * 40 + 9), (1024, 70000)])
 def test_unpack_matches_oracle(dd, oracle_lib, nbits, nchan, nsamp):
     if (nchan * nbits) % 8:
         pytest.skip("spectra must be whole bytes")
@@ -50,7 +51,7 @@ def test_unaligned_input_takes_the_byte_path(dd, oracle_lib, nbits):
         assert np.array_equal(_run(dd, raw, nbits, nchan, nsamp, offset=off), want)
 
 
-@pytest.mark.parametrize("nbits", [8, 2])
+@pytest.mark.parametrize("nbits", [8, 4, 2, 1])
 def test_full_size_lband_block(dd, oracle_lib, nbits):
     """1024 channels x 147628 spectra (the L-band beam's input length)."""
     rng = np.random.default_rng(5 + nbits)
