@@ -621,6 +621,7 @@ def serving_section(dd, torch, dev, seconds: float = 8.0, speed: float = 1.25):
             "copies": {"host_staging_gbs": gbs(st["staging_bytes"], st["staging_ms"]),
                        "h2d_gbs": gbs(st["h2d_bytes"], st["h2d_ms"]),
                        "d2h_gbs": gbs(st["d2h_bytes"], st["d2h_ms"]),
+                       "kernel_ms_per_block": st["kernel_ms"] / max(1, st["completed"]),
                        "per_block_bytes": {"staging": w.nchan * B, "h2d": w.nchan * B,
                                            "d2h": w.ndm * B * 4},
                        "note": "host staging: dd_submit's copy into pinned memory (host "

@@ -424,6 +424,9 @@ typedef struct dd_server_stats {
     int64_t d2h_bytes;       /* result bytes copied device -> host              */
     double d2h_ms;           /* device time of the batches' result copies        */
     int64_t batch_window_us; /* batching window in force                        */
+    double kernel_ms;        /* device time of the batches' kernel phases (from  */
+                             /* the end of the input phase, a wait for SMs the  */
+                             /* other lane's kernel holds included)             */
 } dd_server_stats;
 
 /* A server de-disperses streams of blocks from many beams (the real-time

@@ -62,7 +62,7 @@ class ServerStats(ctypes.Structure):
                 ("staging_bytes", ctypes.c_int64), ("staging_ms", ctypes.c_double),
                 ("h2d_bytes", ctypes.c_int64), ("h2d_ms", ctypes.c_double),
                 ("d2h_bytes", ctypes.c_int64), ("d2h_ms", ctypes.c_double),
-                ("batch_window_us", ctypes.c_int64)]
+                ("batch_window_us", ctypes.c_int64), ("kernel_ms", ctypes.c_double)]
 
     def as_dict(self):
         return {n: getattr(self, n) for n, _ in self._fields_}

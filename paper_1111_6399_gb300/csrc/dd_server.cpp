@@ -201,7 +201,7 @@ struct dd_server_s {
     CopyPool *pool = nullptr;
     std::mutex submit_mu;  // one staging copy at a time through the pool
     int64_t staged_bytes = 0, h2d_bytes = 0, d2h_bytes = 0;  // copy statistics
-    double staged_ms = 0.0, h2d_ms = 0.0, d2h_ms = 0.0;
+    double staged_ms = 0.0, h2d_ms = 0.0, d2h_ms = 0.0, kernel_ms = 0.0;
 };
 
 namespace {
@@ -357,12 +357,14 @@ dd_status start(dd_server_s *v) {
 void account_lane(dd_server_s *v, Lane &l) {
     if (l.accounted)
         return;
-    float ms_in = 0.0f, ms_out = 0.0f;
+    float ms_in = 0.0f, ms_k = 0.0f, ms_out = 0.0f;
     if (cudaEventElapsedTime(&ms_in, l.t[0], l.t[1]) == cudaSuccess &&
+        cudaEventElapsedTime(&ms_k, l.t[1], l.t[2]) == cudaSuccess &&
         cudaEventElapsedTime(&ms_out, l.t[2], l.t[3]) == cudaSuccess) {
         v->h2d_bytes += l.h2d_bytes;
         v->d2h_bytes += l.d2h_bytes;
         v->h2d_ms += ms_in;
+        v->kernel_ms += ms_k;
         v->d2h_ms += ms_out;
     }
     l.accounted = true;
@@ -552,8 +554,13 @@ void worker_main(dd_server_s *v) {
                                                   pick.end();
                                        }),
                         v->queued.end());
-        Lane &l = v->lanes[v->next_lane];
-        v->next_lane ^= 1;
+        // The lane whose last batch has finished, else the next in turn.
+        int li = v->next_lane;
+        if (v->lanes[li].used && cudaEventQuery(v->lanes[li].done) == cudaErrorNotReady &&
+            (!v->lanes[li ^ 1].used || cudaEventQuery(v->lanes[li ^ 1].done) != cudaErrorNotReady))
+            li ^= 1;
+        Lane &l = v->lanes[li];
+        v->next_lane = li ^ 1;
         v->batches++;
         v->batched_blocks += (int64_t)rs.size();
         lk.unlock();
@@ -810,6 +817,7 @@ dd_status dd_server_get_stats(dd_server_t v, dd_server_stats *s) {
     s->h2d_ms = v->h2d_ms;
     s->d2h_bytes = v->d2h_bytes;
     s->d2h_ms = v->d2h_ms;
+    s->kernel_ms = v->kernel_ms;
     s->batch_window_us = v->window_us;
     return DD_OK;
 }
