@@ -126,9 +126,9 @@ __global__ void __launch_bounds__(256) unpack_bytes_kernel(const uint8_t *__rest
 }
 
 // Tiled kernel (see the top of the file).  TT spectra per time tile, NBUF
-// tile buffers in the input ring.
-template <int NBITS, int TT, int NBUF>
-__global__ void __launch_bounds__(256) unpack_tiled_kernel(const uint8_t *__restrict__ in,
+// tile buffers in the input ring, NT threads.
+template <int NBITS, int TT, int NBUF, int NT>
+__global__ void __launch_bounds__(NT) unpack_tiled_kernel(const uint8_t *__restrict__ in,
                                                            int64_t spec_bytes, int64_t nsamp,
                                                            uint8_t *__restrict__ out,
                                                            int64_t out_pitch, int64_t ntile_t) {
@@ -161,7 +161,7 @@ __global__ void __launch_bounds__(256) unpack_tiled_kernel(const uint8_t *__rest
         if (tt < ntile_t) {
             const int rows = rows_of(tt);
             const int64_t t0 = tt * TT;
-            for (int i = threadIdx.x; i < rows * CH; i += 256) {
+            for (int i = threadIdx.x; i < rows * CH; i += NT) {
                 const int r = i / CH, j = i % CH;
                 const uint8_t *src = in + (t0 + r) * spec_bytes + cb0 + 16 * j;
                 const uint32_t dst = sbase + (uint32_t)(b * BUF + r * P + (r >> 2) * 16 + 16 * j);
@@ -187,7 +187,7 @@ __global__ void __launch_bounds__(256) unpack_tiled_kernel(const uint8_t *__rest
         // spectrum hold stale bytes that no store below reaches).
         const int lq = (threadIdx.x & 31) >> 2, lc = threadIdx.x & 3;
         constexpr int NCG = SEG / 16;
-        for (int g = threadIdx.x >> 5; g < (TT / 32) * NCG; g += 8) {
+        for (int g = threadIdx.x >> 5; g < (TT / 32) * NCG; g += NT / 32) {
             const int q = 8 * (g / NCG) + lq;
             const int cw = 4 * (g % NCG) + lc;
             const uint32_t *rp =
@@ -207,7 +207,7 @@ __global__ void __launch_bounds__(256) unpack_tiled_kernel(const uint8_t *__rest
         const int k = (threadIdx.x & 31) % CPR;
         const int64_t t = t0 + 16 * k;
         for (int c = (threadIdx.x >> 5) * RPW + (threadIdx.x & 31) / CPR; c < kTileC;
-             c += 8 * RPW) {
+             c += (NT / 32) * RPW) {
             const uint4 v = *reinterpret_cast<const uint4 *>(turned + c * PO + 16 * (k ^ (2 * swz(c))));
             uint8_t *d = out + (int64_t)(c0 + c) * out_pitch + t;
             if (t + 16 <= nsamp) {
@@ -226,13 +226,14 @@ __global__ void __launch_bounds__(256) unpack_tiled_kernel(const uint8_t *__rest
 }
 
 // Tiled-kernel shape per field width: spectra per time tile, ring buffers,
-// CTAs per SM (measured best on an L-band block of 147628 spectra x 1024
-// channels: 8-bit 5.5 TB/s at (256, 3, 1); 4-bit 5.0, 2-bit and 1-bit
-// 4.4 TB/s at (256, 2, 2)).
+// CTAs per SM, threads (measured best on an L-band block of 147628 spectra
+// x 1024 channels: 8-bit 5.65 TB/s at (256, 3, 1, 512 threads), 5.31 with
+// 256 threads; 4-bit 5.05 and 1-bit 4.62 TB/s at (256, 2, 2, 512)).
 template <int NBITS> struct TiledShape {
     static constexpr int TT = 256;
     static constexpr int NBUF = NBITS == 8 ? 3 : 2;
     static constexpr int CTAS_PER_SM = NBITS == 8 ? 1 : 2;
+    static constexpr int THREADS = 512;
     static constexpr int SMEM = NBUF * (TT * (kTileC * NBITS / 8 + 16) + (TT / 4) * 16) +
                                 kTileC * (TT + 16);
 };
@@ -249,7 +250,7 @@ cudaError_t launch_unpack(const uint8_t *in, int64_t spec_bytes, int nchan, int6
         return e;
     if (tiled) {
         using T = TiledShape<NBITS>;
-        auto k = unpack_tiled_kernel<NBITS, T::TT, T::NBUF>;
+        auto k = unpack_tiled_kernel<NBITS, T::TT, T::NBUF, T::THREADS>;
         static bool configured[64] = {false};
         if (!configured[dev & 63]) {
             e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, T::SMEM);
@@ -260,7 +261,8 @@ cudaError_t launch_unpack(const uint8_t *in, int64_t spec_bytes, int nchan, int6
         const int64_t ntt = (nsamp + T::TT - 1) / T::TT;
         const int64_t want = std::max<int64_t>(1, (int64_t)nsm * T::CTAS_PER_SM / ntc);
         const unsigned gy = (unsigned)std::min<int64_t>(std::min<int64_t>(ntt, want), 65535);
-        k<<<dim3((unsigned)ntc, gy), 256, T::SMEM, s>>>(in, spec_bytes, nsamp, out, out_pitch, ntt);
+        k<<<dim3((unsigned)ntc, gy), T::THREADS, T::SMEM, s>>>(in, spec_bytes, nsamp, out,
+                                                               out_pitch, ntt);
         return cudaGetLastError();
     }
     constexpr int kTileT = tile_t(NBITS);
