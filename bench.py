@@ -65,6 +65,12 @@ PROFILED_TRAFFIC: list[dict] = [
     {"workload": "lowfreq-4096ch-2000dm-262144", "dtype": "f16", "tiles": [4, 12, 1, 12, 8],
      "code_sha256": "81b799d99197287efbc40fdfa738662c596bf5a398684d03d44737ff4d1d8816",
      "bytes": 20705216768 + 2230952960, "compulsory": 2406563840 + 2097152000},
+    # one step, the same beam stored as FP32, tiles (4,6,2,24,8): main launch (1992 DMs) +
+    # remainder (8 DMs)
+    {"workload": "lowfreq-4096ch-2000dm-262144", "dtype": "f32", "tiles": [4, 6, 2, 24, 8],
+     "code_sha256": "81b799d99197287efbc40fdfa738662c596bf5a398684d03d44737ff4d1d8816",
+     "bytes": (86389575424 + 2099985408) + (4307168768 + 7886080),
+     "compulsory": 4813127680 + 2097152000},
     # one step, L-band beam, tiles (4,12,1,8,8): main launch (1008 DMs) + remainder (16 DMs)
     {"workload": "lband-1024ch-1024dm-131072", "dtype": "u8", "tiles": [4, 12, 1, 8, 8],
      "code_sha256": "81b799d99197287efbc40fdfa738662c596bf5a398684d03d44737ff4d1d8816",
