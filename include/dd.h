@@ -230,8 +230,9 @@ dd_status dd_execute_detect(dd_plan_t plan, const void *in, dd_dtype dtype, int6
  * (1, 2, 4 or 8), packed in channel order from the lowest bit of each byte
  * (channel c of spectrum t starts at bit (t*nchan + c)*nbits of the block;
  * bit b is bit b%8 of byte b/8).
- *   in:  device pointer to nsamp*nchan*nbits/8 bytes; any alignment (16-byte
- *        aligned input whose spectra are multiples of 16 bytes is faster).
+ *   in:  device pointer to nsamp*nchan*nbits/8 bytes; any alignment.  Input
+ *        that is 16-byte aligned, with nchan a multiple of 128 and spectra a
+ *        multiple of 16 bytes, takes the faster tiled path.
  *   out: device uint8 [nchan][out_pitch], 16-byte aligned, out_pitch >= nsamp
  *        and a multiple of 16; out[c][t] = the sample (0 .. 2^nbits - 1, not
  *        rescaled).  Columns t >= nsamp are left untouched.
