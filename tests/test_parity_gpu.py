@@ -323,16 +323,32 @@ def _lowfreq_oracle_rows(oracle_lib):
     return _LOWFREQ_CACHE["plane"]
 
 
-@pytest.mark.parametrize("kind", ["u8", "f16", "f32"])
-def test_lowfreq_full_size_half_plane(dd, oracle_lib, kind):
+# Tile shapes of the 4096-channel beam: the ones the bench's autotuner picks
+# (the benchmarked launch; for uint8 also the plan's default) and, for
+# FP16/FP32, the plan's default (None).
+LOWFREQ_TILES = {"u8": [(4, 12, 1, 8, 8)],
+                 "f16": [(4, 12, 1, 12, 8), None],
+                 "f32": [(4, 6, 2, 24, 8), None]}
+
+
+def _lowfreq_plan(dd, dms, dtype, tiles):
+    w = fb.LOWFREQ
+    plan = dd.Plan(w.nchan, w.fch1, w.foff, w.tsamp, dms)
+    if tiles is not None:
+        plan.set_tiles(dtype, *tiles)
+    return plan
+
+
+@pytest.mark.parametrize("kind,tiles", [(k, t) for k, ts in LOWFREQ_TILES.items() for t in ts])
+def test_lowfreq_full_size_half_plane(dd, oracle_lib, kind, tiles):
     """The 4096-channel low-frequency beam at full size (2000 DMs x 262144
-    samples, the benchmarked launch) in each storage type: the same
-    integer-valued noise, so every cell of every second DM row must equal the
-    oracle's exactly (for FP16/FP32 input the oracle's FP64 sums of integers
-    are the same numbers as its uint8 sums)."""
+    samples) in each storage type, in the benchmarked launch (and the default
+    tile shape): the same integer-valued noise, so every cell of every second
+    DM row must equal the oracle's exactly (for FP16/FP32 input the oracle's
+    FP64 sums of integers are the same numbers as its uint8 sums)."""
     w = fb.LOWFREQ
     table, dms, S, data = _lowfreq_input(kind)
-    plan = dd.Plan(w.nchan, w.fch1, w.foff, w.tsamp, dms)
+    plan = _lowfreq_plan(dd, dms, kind, tiles)
     got = _run(dd, plan, data, w.nsamp_out + S, w.nsamp_out)[LOWFREQ_HALF]
     want = _lowfreq_oracle_rows(oracle_lib)
     bad = np.argwhere(got != want)
@@ -350,18 +366,19 @@ LOWFREQ_ROWS = np.unique(np.linspace(0, fb.LOWFREQ.ndm - 1, 64).round().astype(i
 @pytest.mark.parametrize("kind", ["f16-frac", "f32-frac"])
 def test_lowfreq_noninteger_full_length_rows(dd, oracle_lib, kind):
     """Unquantised noise on the 4096-channel band at full size (2000 DMs x
-    262144 samples, the benchmarked launch): 64 DM rows spread over the DM
-    range, every sample of each, within 1e-6 of sum |in| along its curve
-    against the FP64 oracle."""
+    262144 samples), in the benchmarked launch and the default tile shape: 64
+    DM rows spread over the DM range, every sample of each, within 1e-6 of
+    sum |in| along its curve against the FP64 oracle."""
     w = fb.LOWFREQ
     table, dms, S, data = workload_input(w, kind)
-    plan = dd.Plan(w.nchan, w.fch1, w.foff, w.tsamp, dms)
-    got = _run(dd, plan, data, w.nsamp_out + S, w.nsamp_out)
     sel = dms[LOWFREQ_ROWS]
     Ssel = oracle_lib.maxshift(table, sel)
     want, asum = oracle_lib.dedisperse(np.ascontiguousarray(data[:, :w.nsamp_out + Ssel]),
                                        table, sel, w.nsamp_out, with_abssum=True, threads=True)
-    _check_float(got[LOWFREQ_ROWS], want, asum)
+    for tiles in LOWFREQ_TILES[kind[:3]]:
+        plan = _lowfreq_plan(dd, dms, kind[:3], tiles)
+        got = _run(dd, plan, data, w.nsamp_out + S, w.nsamp_out)
+        _check_float(got[LOWFREQ_ROWS], want, asum)
 
 
 def test_launch_count_and_status(dd):
